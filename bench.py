@@ -1,0 +1,289 @@
+"""Benchmark: geodesics/s of the GB300 tracer on the Kerr thin-disk scene
+(a = 0.9, theta_obs = 60 deg, r_obs = 1000 M, 1024 x 1024 camera over
+[-20, 20]^2 M, Dormand-Prince 5(4) at rtol = atol = 1e-10, FP64, disk from the
+ISCO to 30 M with up to 3 crossings).
+
+One step = one full image traced by one persistent launch of the tracer
+(every pixel: initial data, integration, events, crossing refinement,
+emission, constraint monitor).  Rank r of N traces its own image (weak
+scaling, no collective on the data path).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl tartarus|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "geodesics/sec (Kerr a=0.9, 1024², rtol 1e-10) FP64 vs mixed at |H|≤1e-6; % FP peak"
+UNIT = "geodesics/s"
+SM_COUNT = 152
+SM_MAX_MHZ = 2070.0
+# FP64 pipe: 2 DFMA per clock per SM (measured 1.185 TFLOP/s at 1995 MHz with an FMA-chain probe)
+FP64_PEAK_TFLOPS = SM_COUNT * SM_MAX_MHZ * 1e6 * 2 * 2 / 1e12
+# Algorithmic FP64 flops of one Dormand-Prince step attempt on the Kerr FP64 path,
+# counted from the kernel source (FMA = 2, add/mul/div/rcp/sqrt = 1, sin and cos 1 each):
+# 6 flow evaluations x 65 + stage combinations 232 + error norm 20 + step control 5.
+FLOPS_PER_STEP = 6 * 65 + 232 + 20 + 5
+BYTES_OUT_PER_PIXEL = 3 * 3 * 8 + 8 + 8 + 4 + 4 + 1 + 1
+# host-to-device input of one step: the image descriptor (sizeof(tt::ImageDesc)) and the queue reset
+DESC_BYTES = 384 + 8
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="tartarus", choices=["tartarus", "reference"])
+    p.add_argument("--n", type=int, default=1024, help="camera resolution (default: the 1024^2 workload)")
+    p.add_argument("--cpu-seconds", type=float, default=12.0, help="oracle sample budget per measurement")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload(n):
+    from paper_2609_08989_gb300 import scenes
+    return scenes.kerr_disk(n)
+
+
+def config_dict(sc, world):
+    return {"workload": sc.name, "nx": sc.nx, "ny": sc.ny, "a": sc.a, "theta_obs_deg": 60.0,
+            "r_obs": sc.r_obs, "field": [sc.alpha_min, sc.alpha_max], "rtol": sc.rtol, "atol": sc.atol,
+            "integrator": "dopri5", "disk": [ "isco", sc.r_out], "max_crossings": sc.max_crossings,
+            "global_batch": sc.npix * world, "per_gpu_rays": sc.npix, "parallelism": "dp%d" % world,
+            "l2": "flushed between timed steps (256 MiB write); working set is a few MB of state + outputs"}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (the reference arm and the cpu_baseline object)
+# ---------------------------------------------------------------------------
+
+def time_oracle(sc, seconds, seed=7):
+    """Trace seeded random pixels of the scene with the oracle on all host cores
+    until about ``seconds`` of wall time have passed; returns (rays/s, rays, cores)."""
+    import numpy as np
+    import oracle
+    from paper_2609_08989_gb300 import scenes
+    oracle.build()
+    cores = os.cpu_count() or 1
+    rng_seed = seed
+    done, t_used = 0, 0.0
+    chunk = 4096
+    while t_used < seconds:
+        pix = scenes.sample_pixels(sc.npix, chunk, rng_seed)
+        t0 = time.perf_counter()
+        oracle.trace_list(sc, pix, nthreads=cores)
+        dt = time.perf_counter() - t0
+        t_used += dt
+        done += len(pix)
+        rng_seed += 1
+        if dt < 0.5 * seconds:
+            chunk = min(chunk * 2, 1 << 18)
+    return done / t_used, done, cores, t_used
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    sc = workload(args.n)
+    vals = []
+    for _ in range(args.warmup):
+        time_oracle(sc, min(2.0, args.cpu_seconds / 4))
+    tot_rays, tot_t = 0, 0.0
+    for _ in range(args.steps):
+        v, rays, cores, t = time_oracle(sc, args.cpu_seconds / max(1, args.steps) * 2)
+        vals.append(v)
+        tot_rays += rays
+        tot_t += t
+    value = tot_rays / tot_t
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sc.npix / value,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_dict(sc, 1),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": "%d seeded random pixels of the %dx%d image, all host cores"
+                                       % (tot_rays, sc.nx, sc.ny)},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        for line in open(self.f.name):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        import statistics
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def run_tartarus(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from paper_2609_08989_gb300 import tartarus as T
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    sc = workload(args.n)
+    T.lib()
+    out = T.alloc_outputs(sc.npix)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    for k in range(max(args.warmup, 0)):
+        flush.fill_(k & 0xFF)                     # first touch of the flush buffer stays out of the timing
+        T.trace(sc, out=out)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    launches0 = T.launch_count()
+    step_attempts = 0
+    barrier()
+    clocks.start()
+    t_begin = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_begin.record(stream)
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)                     # L2 flush between timed steps
+        ev[k][0].record(stream)
+        T.trace(sc, out=out, stream=stream)
+        ev[k][1].record(stream)
+    t_end.record(stream)
+    barrier()
+    clk = clocks.stop()
+    launches = T.launch_count() - launches0
+    step_attempts = int(out["steps"].sum().item() + out["rejects"].sum().item())
+    total_ms = t_begin.elapsed_time(t_end)
+    kern_ms = [a.elapsed_time(b) for a, b in ev]
+    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+    value = world * sc.npix * args.steps / (total_ms / 1e3)
+    mean_kern = sum(kern_ms) / len(kern_ms)
+
+    # end to end through the host-buffer entry point (outputs copied to pinned host memory)
+    host = T.alloc_host_outputs(sc.npix)
+    T.trace_host(sc, out=host)
+    barrier()
+    e0 = time.perf_counter()
+    for _ in range(args.steps):
+        T.trace_host(sc, out=host)
+        _ = float(host["intensity"][0])           # the host reads the result
+    barrier()
+    e2e_s = time.perf_counter() - e0
+    tt = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    e2e_value = world * sc.npix * args.steps / float(tt.item())
+
+    if rank == 0:
+        flops = FLOPS_PER_STEP * step_attempts
+        achieved = flops / (mean_kern / 1e3) / 1e12
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_dict(sc, world),
+            "rk_steps_per_s": world * step_attempts * args.steps / (total_ms / 1e3),
+            "rk_step_attempts_per_image": step_attempts,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                         "kernel": "trace_kernel64<0>", "kernel_ms": mean_kern,
+                         "peak_source": "FP64 pipe: 152 SMs x 2070 MHz x 2 DFMA/clk (derived)",
+                         "flops_per_unit": FLOPS_PER_STEP, "unit_of_work": "Dormand-Prince step attempt"},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": DESC_BYTES,
+                    "d2h_bytes_per_step": BYTES_OUT_PER_PIXEL * sc.npix},
+            "gpu_launches": launches,
+            "clocks": clk,
+        }
+        if not args.no_cpu_baseline:
+            v, rays, cores, tsec = time_oracle(sc, args.cpu_seconds)
+            line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                    "sample": "%d seeded random pixels of the %dx%d image (%.1f s)"
+                                              % (rays, sc.nx, sc.ny, tsec)}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_tartarus(args)
+
+
+if __name__ == "__main__":
+    main()

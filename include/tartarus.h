@@ -1,0 +1,214 @@
+/*
+ * tartarus.h -- C ABI of the GB300 geodesic ray tracer.
+ *
+ * Backward tracing of one null geodesic per image-plane pixel from a distant
+ * observer through a Kerr metric (closed form) or a tabulated (r, theta)
+ * metric, after TARTARUS (arXiv 2609.08989):
+ *   - Hamiltonian flow H = 1/2 g^{mu nu} p_mu p_nu, H = 0            (Sec. 2.1)
+ *   - initial momenta from the ZAMO tetrad at (r_obs, theta_obs)     (Sec. 2.2)
+ *   - adaptive Dormand-Prince 5(4) with horizon / escape / disk events (Sec. 3.2)
+ *   - Page-Thorne flux F(r), redshift g and I = g^4 F at crossings    (Sec. 2.3-2.4)
+ *   - the constraint residual |H| monitored after every accepted step (Sec. 4.1)
+ *
+ * Conventions.  Geometric units G = c = 1, Boyer-Lindquist coordinates.
+ * The state integrated is the time-reversed photon: p_mu -> -p_mu of the
+ * physical, future-directed momentum, with the affine parameter increasing.
+ * A pixel (i, j) of an nx x ny camera sits at the cell centre
+ *   alpha = alpha_min + (i + 1/2) (alpha_max - alpha_min) / nx,
+ *   beta  = beta_min  + (j + 1/2) (beta_max  - beta_min)  / ny,
+ * and has the linear index p = j nx + i.
+ *
+ * Errors.  Every entry point returns 0 (TT_OK) or a negative TT_E* code; no
+ * exception or abort crosses the ABI.  Invalid arguments are reported before
+ * anything is launched.  Numerical failures of single rays are not call
+ * errors: they are per-pixel termination codes (TT_CODE_*).
+ *
+ * Ownership.  The caller owns every output buffer and every descriptor.  The
+ * library owns the device copies of metric tables (until
+ * tartarus_table_destroy) and a small per-device work-queue buffer that lives
+ * until the process exits.
+ *
+ * Streams.  Work is enqueued on the CUDA stream passed in (NULL = the legacy
+ * default stream) and returns without synchronising, except the *_host entry
+ * point, which synchronises its stream before returning.
+ */
+#ifndef TARTARUS_H
+#define TARTARUS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define TT_OK            0
+#define TT_EINVAL       -1   /* an argument is out of range; nothing launched   */
+#define TT_ENOMEM       -2   /* a device or pinned allocation failed            */
+#define TT_ECUDA        -3   /* a CUDA runtime call failed (see error string)   */
+#define TT_EUNSUPPORTED -4   /* the request names a variant that is not built   */
+
+/* ---- per-pixel termination codes (int8) ------------------------------- */
+#define TT_CODE_ESCAPED   0  /* r > escape_factor * r_obs (paper Sec. 3.2, C_E)            */
+#define TT_CODE_CAPTURED  1  /* r < r_h (1 + horizon_eps) (paper Sec. 3.2, C_H)            */
+#define TT_CODE_MAXSTEPS  2  /* accepted + rejected steps reached max_steps                */
+#define TT_CODE_UNDERFLOW 3  /* step size fell below h_min                                  */
+#define TT_CODE_NONFINITE 4  /* a NaN or Inf appeared in the state or the error estimate    */
+#define TT_CODE_BADPIXEL  5  /* alpha^2 + beta^2 >= r_obs^2, or a non-finite pixel position  */
+
+#define TT_MAX_CROSSINGS 3   /* disk crossings stored per pixel */
+
+/* ---- enumerations ---------------------------------------------------- */
+#define TT_METRIC_KERR   0
+#define TT_METRIC_TABLE  1
+#define TT_DP54          0   /* Dormand-Prince 5(4) (paper Sec. 3.2)   */
+#define TT_FP64          0   /* all arithmetic in binary64             */
+#define TT_MIXED         1   /* FP32 stages, FP64 state accumulation   */
+#define TT_REFINE_HENON   0  /* exact step onto theta = pi/2 (default) */
+#define TT_REFINE_HERMITE 1  /* paper's cubic-Hermite bisection        */
+
+typedef struct tt_table tt_table;        /* opaque device copy of a metric table */
+
+/* Spacetime.  kind TT_METRIC_KERR: mass M > 0, spin |a| < M.
+ * kind TT_METRIC_TABLE: 'table' from tartarus_table_create; M and a are then
+ * used only by the disk model (ISCO, Keplerian Omega, Page-Thorne flux). */
+typedef struct {
+    int kind;
+    double M, a;
+    const tt_table *table;
+} tt_metric;
+
+/* Observer at r_obs > 0 and inclination 0 < theta_obs < pi (radians). */
+typedef struct {
+    double r_obs, theta_obs;
+} tt_observer;
+
+/* Camera grid; pixels [pix_begin, pix_begin + pix_count) are traced and written
+ * to outputs index 0 .. pix_count-1.  pix_count <= 0 means "to the end". */
+typedef struct {
+    int nx, ny;
+    double alpha_min, alpha_max, beta_min, beta_max;
+    long long pix_begin, pix_count;
+} tt_camera;
+
+/* Integrator (paper Sec. 3.2).  rtol, atol > 0.  h0 <= 0: automatic start step
+ * (Hairer-Norsett-Wanner starting-step algorithm).  h_min <= 0: 1e-14 max(1, |lambda|).
+ * max_steps >= 1 caps accepted + rejected steps.  Captured when
+ * r < r_h (1 + horizon_eps), escaped when r > escape_factor * r_obs
+ * (escape_factor > 1).  fp64_radius_factor (mixed only): steps that start at
+ * r < fp64_radius_factor * r_h run in FP64 (<= 0 selects 1.5). */
+typedef struct {
+    int method;                 /* TT_DP54 */
+    int precision;              /* TT_FP64 or TT_MIXED */
+    double rtol, atol, h0, h_min;
+    long long max_steps;
+    double horizon_eps, escape_factor;
+    int refine;                 /* TT_REFINE_HENON or TT_REFINE_HERMITE */
+    double fp64_radius_factor;
+} tt_solver;
+
+/* Thin disk in the equatorial plane (paper Sec. 2.3).  r_in <= 0 selects the
+ * prograde ISCO (requires a >= 0).  max_crossings in 0..3 are stored; all
+ * crossings with r_in <= r <= r_out are counted.  doppler = 0 drops the
+ * Omega p_phi term of the redshift (paper Fig. 3b). */
+typedef struct {
+    int enabled;
+    double r_in, r_out, mdot;
+    int max_crossings;
+    int doppler;
+} tt_disk;
+
+/* Outputs: caller-owned DEVICE buffers of pix_count elements, except the three
+ * crossing arrays, which hold 3 * pix_count doubles, crossing-major (crossing k
+ * of output pixel q at [k * pix_count + q]).  Unused crossing slots are 0.
+ *   code       int8  termination code
+ *   n_cross    int8  number of in-range crossings (saturates at 127)
+ *   r_cross    f64   crossing radius
+ *   g          f64   redshift factor nu_obs / nu_em
+ *   I_cross    f64   g^4 F(r)
+ *   intensity  f64   sum of I_cross over the stored crossings
+ *   h_max      f64   max |H| over the initial state and every accepted step
+ *   steps      int32 accepted steps
+ *   rejects    int32 rejected steps                                      */
+typedef struct {
+    int8_t *code;
+    int8_t *n_cross;
+    double *r_cross;
+    double *g;
+    double *I_cross;
+    double *intensity;
+    double *h_max;
+    int32_t *steps;
+    int32_t *rejects;
+} tt_outputs;
+
+/* Launch shape; NULL or zero fields select the tuned defaults.
+ *   block        threads per block (multiple of 32, 32..1024)
+ *   reg_variant  0: default register cap, 1..4: tighter caps (64/80/96/128 regs)
+ *   refill       refill idle lanes when at least this many lanes of a warp are idle (1..32)
+ *   blocks_per_sm  persistent blocks per SM (0: from occupancy) */
+typedef struct {
+    int block;
+    int reg_variant;
+    int refill;
+    int blocks_per_sm;
+} tt_tune;
+
+/* Trace one camera (paper Sec. 3.1 execution flow, steps 1-6): every pixel of
+ * the range gets its initial data, is integrated to a terminal event, and has
+ * its crossings refined and their emission evaluated.  Asynchronous on stream.
+ * Returns TT_EINVAL for inconsistent arguments (nothing launched), TT_ECUDA if
+ * the launch fails. */
+int tartarus_trace(const tt_metric *metric, const tt_observer *obs, const tt_camera *cam,
+                   const tt_solver *solver, const tt_disk *disk, const tt_outputs *out,
+                   const tt_tune *tune, void *cuda_stream);
+
+/* Same as tartarus_trace, but the outputs are HOST buffers (pinned memory is
+ * fastest): the library traces into device buffers it owns and copies the
+ * results back; it synchronises the stream before returning. */
+int tartarus_trace_host(const tt_metric *metric, const tt_observer *obs, const tt_camera *cam,
+                        const tt_solver *solver, const tt_disk *disk, const tt_outputs *host_out,
+                        const tt_tune *tune, void *cuda_stream);
+
+/* One image of a batch. */
+typedef struct {
+    tt_metric metric;
+    tt_observer obs;
+    tt_camera cam;
+    tt_disk disk;
+    tt_outputs out;
+} tt_image;
+
+/* Trace n images of uneven size, spin and inclination in ONE persistent launch
+ * that pulls rays from a shared queue (replaces the paper's per-pixel thread
+ * pool, Sec. 4.3).  All images share the solver settings.  An image whose
+ * descriptor is invalid is skipped and reported in status[i] (TT_EINVAL) if
+ * status is not NULL; the call then returns TT_EINVAL but still traces the
+ * valid images.  Asynchronous on stream. */
+int tartarus_trace_batch(const tt_image *images, int n, const tt_solver *solver,
+                         const tt_tune *tune, int *status, void *cuda_stream);
+
+/* Copy a metric table to the device (paper: numerically generated metrics).
+ * host_nodes holds nth * nr * 20 doubles: node (j, k) at [(j nr + k) 20], with
+ * r_k = r_min (r_max / r_min)^(k/(nr-1)) and theta_j = pi j / (nth-1); for each
+ * field F in (g_tt, g_tphi, g_thth, g_phiphi, g^rr) the four numbers
+ * F, dF/dr, dF/dtheta, d2F/(dr dtheta).  r_min is taken as the horizon.
+ * Interpolation is bicubic Hermite in (ln r, theta).  nr, nth >= 2,
+ * 0 < r_min < r_max.  The host array may be freed after the call. */
+int tartarus_table_create(const double *host_nodes, int nr, int nth, double r_min, double r_max,
+                          tt_table **out);
+int tartarus_table_destroy(tt_table *table);
+
+/* Static description of a status code. */
+const char *tartarus_error_string(int status);
+
+/* Number of kernels this library has launched in this process. */
+long long tartarus_launch_count(void);
+
+/* Version string. */
+const char *tartarus_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TARTARUS_H */

@@ -1,0 +1,283 @@
+// tt_device.cuh -- device arithmetic of the geodesic tracer (sm_103a).
+//
+// One ray per thread.  The state carried through the integrator is the
+// dynamical core (r, theta, p_r, p_theta) of the paper's 8-dimensional
+// phase-space array (Sec. 2.1): p_t and p_phi are constants of the motion and
+// t, phi never feed back into the flow, so they are not integrated.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "tt_internal.h"
+
+namespace tt {
+
+constexpr double kHalfPi = 1.5707963267948966;   // binary64 pi/2
+
+// ---------------------------------------------------------------------------
+// Reciprocal: the SFU's approximate double reciprocal refined by two Newton-
+// Raphson steps y <- y (2 - x y); each step squares the relative error, so the
+// result is within about one ulp of 1/x for normal x.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double rcp64(double x) {
+    double y;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+    double e = fma(-x, y, 1.0);
+    y = fma(y, e, y);
+    e = fma(-x, y, 1.0);
+    return fma(y, e, y);
+}
+
+// Per-ray constants of the (time-reversed) photon.
+struct RayConst {
+    double pt, pph;       // p_t, p_phi
+    double apph;          // a p_phi
+    double pph2;          // p_phi^2
+    double a2pt2;         // a^2 p_t^2
+    double c0;            // 2 a p_t p_phi
+};
+
+__device__ __forceinline__ RayConst make_ray_const(double a, double pt, double pph) {
+    RayConst R;
+    R.pt = pt;
+    R.pph = pph;
+    R.apph = a * pph;
+    R.pph2 = pph * pph;
+    R.a2pt2 = a * a * pt * pt;
+    R.c0 = 2.0 * a * pt * pph;
+    return R;
+}
+
+struct State {
+    double r, th, pr, pth;
+};
+
+// ---------------------------------------------------------------------------
+// Kerr flow.  H = K / (2 Sigma) with Carter's separated form of g^{mu nu} p p,
+//   K = Delta p_r^2 + p_th^2 + (p_phi + a p_t sin^2)^2 / sin^2
+//       - ((r^2 + a^2) p_t + a p_phi)^2 / Delta,
+// so dr = Delta p_r / Sigma, dth = p_th / Sigma and
+//   dp_r  = -(dK/dr  - 4 r H) / (2 Sigma),
+//   dp_th = -(dK/dth + 4 a^2 sin cos H) / (2 Sigma),
+// Hamilton's equations of Sec. 2.1 exactly (the H terms keep the flow exact
+// off the constraint surface).  One reciprocal serves 1/Sigma, 1/Delta and
+// 1/sin^2.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void kerr_flow64(double M, double a, const RayConst& R, const State& y,
+                                            State& f, double& H) {
+    double s, c;
+    sincos(y.th, &s, &c);
+    const double a2 = a * a;
+    const double r = y.r;
+    double s2 = s * s, c2 = c * c, sc = s * c;
+    double r2 = r * r;
+    double Sig = fma(a2, c2, r2);
+    double Del = fma(r, r - 2.0 * M, a2);
+    double A = fma(r2 + a2, R.pt, R.apph);
+    double SD = Sig * Del;
+    double inv = rcp64(SD * s2);
+    double iS = inv * (Del * s2);
+    double iD = inv * (Sig * s2);
+    double u = inv * SD;
+    double pr2 = y.pr * y.pr;
+    double AiD = A * iD;
+    double K = fma(R.a2pt2, s2, R.c0);
+    K = fma(R.pph2, u, K);
+    K = fma(y.pth, y.pth, K);
+    K = fma(Del, pr2, K);
+    K = fma(-A, AiD, K);
+    H = 0.5 * K * iS;
+    double dKr = fma(2.0 * (r - M), fma(AiD, AiD, pr2), -4.0 * r * R.pt * AiD);
+    double dKt = 2.0 * sc * fma(-R.pph2, u * u, R.a2pt2);
+    double hiS = 0.5 * iS;
+    f.r = Del * iS * y.pr;
+    f.th = y.pth * iS;
+    f.pr = fma(4.0 * r, H, -dKr) * hiS;
+    f.pth = -fma(4.0 * a2 * sc, H, dKt) * hiS;
+}
+
+// Kerr g_tt, g_tphi, g_rr, g_thth, g_phiphi (Boyer-Lindquist).
+__device__ __forceinline__ void kerr_lower64(double M, double a, double r, double th, double g[5]) {
+    double s, c;
+    sincos(th, &s, &c);
+    double s2 = s * s;
+    double Sig = r * r + a * a * c * c;
+    double Del = r * r - 2.0 * M * r + a * a;
+    g[0] = -(1.0 - 2.0 * M * r / Sig);
+    g[1] = -2.0 * M * a * r * s2 / Sig;
+    g[2] = Sig / Del;
+    g[3] = Sig;
+    g[4] = (r * r + a * a + 2.0 * M * a * a * r * s2 / Sig) * s2;
+}
+
+// ---------------------------------------------------------------------------
+// Tabulated metric: bicubic Hermite patches in (u = ln r, theta).  Device nodes
+// hold, per field, (F, F_u du, F_th dth, F_uth du dth) -- slopes already in the
+// unit-cell coordinates -- so a patch is a plain tensor-product Hermite form.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void hermite4(double t, double h[4], double dh[4]) {
+    double t2 = t * t, omt = 1.0 - t;
+    h[0] = (1.0 + 2.0 * t) * omt * omt;
+    h[1] = t * omt * omt;
+    h[2] = t2 * (3.0 - 2.0 * t);
+    h[3] = t2 * (t - 1.0);
+    dh[0] = 6.0 * t2 - 6.0 * t;
+    dh[1] = fma(3.0, t2, fma(-4.0, t, 1.0));
+    dh[2] = 6.0 * t - 6.0 * t2;
+    dh[3] = fma(3.0, t2, -2.0 * t);
+}
+
+// All five fields (g_tt, g_tphi, g_thth, g_phiphi, g^rr) with d/dr and d/dth.
+__device__ __forceinline__ void table_fields64(const ImageDesc& d, double r, double th,
+                                               double f[5], double fr[5], double ft[5]) {
+    double tu = (log(r) - d.u0) / d.du;
+    double tw = th / d.dth;
+    int k = (int)floor(tu), j = (int)floor(tw);
+    k = min(max(k, 0), d.nr - 2);
+    j = min(max(j, 0), d.nth - 2);
+    double t = tu - (double)k, w = tw - (double)j;
+    double A[4], dA[4], B[4], dB[4];
+    hermite4(t, A, dA);
+    hermite4(w, B, dB);
+    const double* n00 = d.table + ((size_t)j * d.nr + k) * kTableNF;
+    const double* nodes[4] = {n00, n00 + kTableNF, n00 + (size_t)d.nr * kTableNF,
+                              n00 + (size_t)d.nr * kTableNF + kTableNF};
+    // node order: (k, j), (k+1, j), (k, j+1), (k+1, j+1) -> (cu, ct) = (0,0), (1,0), (0,1), (1,1)
+    const double inv_dur = 1.0 / (d.du * r), inv_dth = 1.0 / d.dth;
+#pragma unroll
+    for (int fi = 0; fi < 5; ++fi) {
+        double v = 0.0, vu = 0.0, vt = 0.0;
+#pragma unroll
+        for (int nd = 0; nd < 4; ++nd) {
+            const int cu = nd & 1, ct = nd >> 1;
+            const double2* p = reinterpret_cast<const double2*>(nodes[nd] + 4 * fi);
+            double2 q0 = __ldg(p), q1 = __ldg(p + 1);     // (F, Fu), (Ft, Fut)
+            double a0 = A[2 * cu], a1 = A[2 * cu + 1], da0 = dA[2 * cu], da1 = dA[2 * cu + 1];
+            double b0 = B[2 * ct], b1 = B[2 * ct + 1], db0 = dB[2 * ct], db1 = dB[2 * ct + 1];
+            double cb = fma(q0.x, b0, q1.x * b1);          // value column along theta
+            double cub = fma(q0.y, b0, q1.y * b1);         // u-slope column along theta
+            double cdb = fma(q0.x, db0, q1.x * db1);
+            double cudb = fma(q0.y, db0, q1.y * db1);
+            v = fma(a0, cb, fma(a1, cub, v));
+            vu = fma(da0, cb, fma(da1, cub, vu));
+            vt = fma(a0, cdb, fma(a1, cudb, vt));
+        }
+        f[fi] = v;
+        fr[fi] = vu * inv_dur;
+        ft[fi] = vt * inv_dth;
+    }
+}
+
+// Flow of H = 1/2 [W/D + g^rr p_r^2 + p_th^2 / g_thth], with the inverse of the
+// (t, phi) block, D = g_tt g_phiphi - g_tphi^2,
+// W = g_phiphi p_t^2 - 2 g_tphi p_t p_phi + g_tt p_phi^2.
+__device__ __forceinline__ void table_flow64(const ImageDesc& d, const RayConst& R, const State& y,
+                                             State& f, double& H) {
+    double F[5], Fr[5], Ft[5];
+    table_fields64(d, y.r, y.th, F, Fr, Ft);
+    const double pt2 = R.pt * R.pt, ptp = 2.0 * R.pt * R.pph;
+    double D = fma(F[0], F[3], -F[1] * F[1]);
+    double iD = rcp64(D);
+    double W = fma(F[3], pt2, fma(-F[1], ptp, F[0] * R.pph2));
+    double WiD = W * iD;
+    double ith = rcp64(F[2]);
+    double pr2 = y.pr * y.pr, pth2 = y.pth * y.pth;
+    H = 0.5 * (WiD + fma(F[4], pr2, pth2 * ith));
+    double dW_r = fma(Fr[3], pt2, fma(-Fr[1], ptp, Fr[0] * R.pph2));
+    double dD_r = fma(Fr[0], F[3], fma(F[0], Fr[3], -2.0 * F[1] * Fr[1]));
+    double dW_t = fma(Ft[3], pt2, fma(-Ft[1], ptp, Ft[0] * R.pph2));
+    double dD_t = fma(Ft[0], F[3], fma(F[0], Ft[3], -2.0 * F[1] * Ft[1]));
+    double ith2 = ith * ith;
+    double d2H_r = fma(-WiD, dD_r, dW_r) * iD + fma(Fr[4], pr2, -Fr[2] * ith2 * pth2);
+    double d2H_t = fma(-WiD, dD_t, dW_t) * iD + fma(Ft[4], pr2, -Ft[2] * ith2 * pth2);
+    f.r = F[4] * y.pr;
+    f.th = y.pth * ith;
+    f.pr = -0.5 * d2H_r;
+    f.pth = -0.5 * d2H_t;
+}
+
+__device__ __forceinline__ void table_lower64(const ImageDesc& d, double r, double th, double g[5]) {
+    double F[5], Fr[5], Ft[5];
+    table_fields64(d, r, th, F, Fr, Ft);
+    g[0] = F[0];
+    g[1] = F[1];
+    g[2] = 1.0 / F[4];
+    g[3] = F[2];
+    g[4] = F[3];
+}
+
+// METRIC: 0 closed-form Kerr, 1 table, 2 chosen per image at run time.
+template <int METRIC>
+__device__ __forceinline__ void flow64(const ImageDesc& d, double M, double a, const RayConst& R,
+                                       const State& y, State& f, double& H) {
+    if (METRIC == 0 || (METRIC == 2 && d.kind == 0)) kerr_flow64(M, a, R, y, f, H);
+    else table_flow64(d, R, y, f, H);
+}
+
+template <int METRIC>
+__device__ __forceinline__ void lower64(const ImageDesc& d, double r, double th, double g[5]) {
+    if (METRIC == 0 || (METRIC == 2 && d.kind == 0)) kerr_lower64(d.M, d.a, r, th, g);
+    else table_lower64(d, r, th, g);
+}
+
+// ---------------------------------------------------------------------------
+// Page-Thorne flux (paper Sec. 2.3, prefactor as printed) with the host-resolved
+// roots and coefficients; zero inside the ISCO.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double flux64(const ImageDesc& d, double r) {
+    double x = sqrt(r / d.M);
+    if (x < d.fx0) return 0.0;
+    double sum = 0.0;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+        if (d.fcoef[i] != 0.0) sum = fma(d.fcoef[i], log(x - d.fxr[i]) - d.flog0[i], sum);
+    double br = x - d.fx0 - 1.5 * d.fa * log(x / d.fx0) - sum;
+    double x2 = x * x;
+    double pref = 3.0 / (2.0 * x2 * x2 * (x2 * x - 3.0 * x + 2.0 * d.fa));
+    return d.flux_scale * pref * br;
+}
+
+// Redshift g = p_t / (u^t (p_t + Omega p_phi)) of a prograde Keplerian emitter
+// (paper Sec. 2.4); Doppler off: g = 1 / u^t.
+template <int METRIC>
+__device__ __forceinline__ double redshift64(const ImageDesc& d, double r, double pt, double pph) {
+    double g[5];
+    if (METRIC == 0 || (METRIC == 2 && d.kind == 0)) {
+        double M = d.M, a = d.a;
+        g[0] = -(1.0 - 2.0 * M / r);
+        g[1] = -2.0 * M * a / r;
+        g[4] = r * r + a * a + 2.0 * M * a * a / r;
+    } else {
+        lower64<METRIC>(d, r, kHalfPi, g);
+    }
+    double Om = d.sqrtM / (r * sqrt(r) + d.a * d.sqrtM);
+    double ut = 1.0 / sqrt(-g[0] - 2.0 * Om * g[1] - Om * Om * g[4]);
+    if (!d.doppler) return 1.0 / ut;
+    return pt / (ut * (pt + Om * pph));
+}
+
+// ---------------------------------------------------------------------------
+// Dormand-Prince 5(4) coefficients (Dormand & Prince 1980).
+// ---------------------------------------------------------------------------
+namespace dp {
+constexpr double c2 = 1.0 / 5.0, c3 = 3.0 / 10.0, c4 = 4.0 / 5.0, c5 = 8.0 / 9.0;
+constexpr double a21 = 1.0 / 5.0;
+constexpr double a31 = 3.0 / 40.0, a32 = 9.0 / 40.0;
+constexpr double a41 = 44.0 / 45.0, a42 = -56.0 / 15.0, a43 = 32.0 / 9.0;
+constexpr double a51 = 19372.0 / 6561.0, a52 = -25360.0 / 2187.0, a53 = 64448.0 / 6561.0,
+                 a54 = -212.0 / 729.0;
+constexpr double a61 = 9017.0 / 3168.0, a62 = -355.0 / 33.0, a63 = 46732.0 / 5247.0,
+                 a64 = 49.0 / 176.0, a65 = -5103.0 / 18656.0;
+constexpr double b1 = 35.0 / 384.0, b3 = 500.0 / 1113.0, b4 = 125.0 / 192.0,
+                 b5 = -2187.0 / 6784.0, b6 = 11.0 / 84.0;
+// e = b - bhat
+constexpr double e1 = 35.0 / 384.0 - 5179.0 / 57600.0;
+constexpr double e3 = 500.0 / 1113.0 - 7571.0 / 16695.0;
+constexpr double e4 = 125.0 / 192.0 - 393.0 / 640.0;
+constexpr double e5 = -2187.0 / 6784.0 + 92097.0 / 339200.0;
+constexpr double e6 = 11.0 / 84.0 - 187.0 / 2100.0;
+constexpr double e7 = -1.0 / 40.0;
+}  // namespace dp
+
+}  // namespace tt

@@ -1,0 +1,137 @@
+"""Element-by-element comparison of CUDA outputs with the oracle's.
+
+Rules (FP64 path):
+  * termination codes bit-exact, except pixels within the +-1e-6 band around
+    the critical curve (classified independently with the radial quartic);
+  * crossing counts equal, except band pixels and crossings whose radius lies
+    within 1e-8 (relative) of the disk edges;
+  * radii and g factors within ``rel`` (relative) -- or ``rel_diverged`` for
+    rays whose step counts differ, where a rounding-level accept/reject flip
+    made the two sides take different valid step sequences; per-crossing and summed
+    intensities within ``rel`` of (value + the image's peak), because F(r)
+    vanishes at the ISCO; unused slots exactly 0;
+  * |H| maxima (an error measure itself): within 5% on escaped rays; within a
+    factor 2 on rays that end at the horizon, where |p_r| ~ 1/(r - r_h) makes
+    H sensitive to last-bit differences of the two equivalent flow formulas,
+    and on diverged rays when ``rel_diverged`` is given.
+"""
+import math
+
+import numpy as np
+
+import kerr_exact as KE
+
+FIELDS = ("r_cross", "g", "I_cross")
+
+
+def pixel_ab(sc, pix):
+    i = pix % sc.nx
+    j = pix // sc.nx
+    al = sc.alpha_min + (i + 0.5) * ((sc.alpha_max - sc.alpha_min) / sc.nx)
+    be = sc.beta_min + (j + 0.5) * ((sc.beta_max - sc.beta_min) / sc.ny)
+    return al, be
+
+
+def in_band(orc, sc, pix, width=None):
+    """True if the pixel's capture class changes under moves of alpha or beta by
+    +-width (1e-6 for the closed-form metric).  A tabulated metric is classified
+    with the Kerr spacetime it samples and a band of 1e-4, since interpolation
+    (~1e-6 relative) shifts its critical curve."""
+    if width is None:
+        width = 1e-6 if sc.metric_kind == 0 else 1e-4
+    sc = sc.replace(metric_kind=0, table=None) if sc.metric_kind != 0 else sc
+    r_stop = orc.rplus(sc.M, sc.a) * (1 + sc.horizon_eps)
+    al, be = pixel_ab(sc, pix)
+
+    def klass(a_, b_):
+        y = orc.initial_state(sc, a_, b_)
+        p = -y[4:]
+        E, L = -p[0], p[3]
+        Q = p[2] ** 2 + math.cos(sc.theta_obs) ** 2 * (-sc.a ** 2 * E * E + L * L / math.sin(sc.theta_obs) ** 2)
+        return KE.classify(sc.a / sc.M, L / E, Q / E ** 2, r_stop, sc.r_obs)
+
+    c0 = klass(al, be)
+    return any(klass(al + dx, be + dy) != c0 for dx, dy in ((width, 0), (-width, 0), (0, width), (0, -width)))
+
+
+def compare(orc, sc, got, ref, pix, rel=1e-9, h_abs=1e-12, h_rel=5e-2, min_same_steps=0.98, report=None,
+            rel_diverged=None):
+    """got/ref: dicts of numpy arrays for pixel indices pix (same order).
+
+    rel_diverged: tolerance for rays whose accepted/rejected step counts differ
+    between the two sides (an accept/reject decision taken at err ~ 1 within
+    rounding went the other way, so the two are different valid integrations);
+    None means such rays get ``rel`` too."""
+    pix = np.asarray(pix)
+    n = len(pix)
+    code_bad = np.nonzero(got["code"] != ref["code"])[0]
+    band = set(int(q) for q in code_bad if in_band(orc, sc, int(pix[q])))
+    unexplained = [int(q) for q in code_bad if int(q) not in band]
+    assert not unexplained, "codes differ outside the band at pixels %s" % pix[unexplained[:10]]
+    ok = got["code"] == ref["code"]
+    r_in = sc.r_in if sc.r_in > 0 else None
+    nc_bad = np.nonzero(ok & (got["n_cross"] != ref["n_cross"]))[0]
+    for q in nc_bad:
+        radii = [x for x in list(ref["r_cross"][:, q]) + list(got["r_cross"][:, q]) if x != 0]
+        edges = [sc.r_out] + ([r_in] if r_in else [orc.isco(sc.M, sc.a)])
+        near_edge = any(abs(x - e) <= 1e-8 * e for x in radii for e in edges)
+        assert near_edge or in_band(orc, sc, int(pix[q])), \
+            "crossing count differs at pixel %d: %d vs %d" % (pix[q], got["n_cross"][q], ref["n_cross"][q])
+    same = ok & (got["n_cross"] == ref["n_cross"])
+    worst = {}
+    peak = float(np.abs(ref["I_cross"]).max()) if ref["I_cross"].size else 0.0
+    # near-critical rays (photon-ring orbits) amplify last-bit differences
+    # exponentially in the number of half-orbits: crossing values of band
+    # pixels are exempt, like their codes
+    with np.errstate(divide="ignore", invalid="ignore"):
+        prel = np.where(ref["r_cross"] != 0, np.abs(got["r_cross"] - ref["r_cross"]) / np.abs(ref["r_cross"]), 0.0)
+    diverged = (got["steps"] != ref["steps"]) | (got["rejects"] != ref["rejects"])
+    tol_px = np.where(diverged & (rel_diverged is not None), rel_diverged if rel_diverged else rel, rel)
+    for q in np.nonzero(same & (prel.max(axis=0) > tol_px))[0]:
+        if in_band(orc, sc, int(pix[q])):
+            same[q] = False
+            band.add(int(q))
+        else:
+            print("crossing mismatch outside the band: pixel", int(pix[q]), "got", got["r_cross"][:, q],
+                  "ref", ref["r_cross"][:, q], "steps", got["steps"][q], ref["steps"][q])
+    for label, sel, tol in (("", same & ~diverged, rel), ("_diverged", same & diverged,
+                                                            rel_diverged if rel_diverged else rel)):
+        for f in FIELDS:
+            a, b = got[f][:, sel], ref[f][:, sel]
+            zero = b == 0
+            assert np.array_equal(a[zero], b[zero]), "%s: unused slots differ" % f
+            if f == "I_cross":
+                # F(r) vanishes at the ISCO, where the relative error of g^4 F is amplified
+                # by r F'/F: compare against rel of the value plus rel of the image's peak
+                d = np.abs(a[~zero] - b[~zero]) / (np.abs(b[~zero]) + peak)
+            else:
+                d = np.abs(a[~zero] - b[~zero]) / np.abs(b[~zero])
+            worst[f + label] = float(d.max()) if d.size else 0.0
+            assert worst[f + label] <= tol, "%s%s: max rel err %.3e > %.1e" % (f, label, worst[f + label], tol)
+        a, b = got["intensity"][sel], ref["intensity"][sel]
+        nz = b != 0
+        assert np.array_equal(a[~nz], b[~nz])
+        di = np.abs(a[nz] - b[nz]) / (np.abs(b[nz]) + peak)
+        worst["intensity" + label] = float(di.max()) if di.size else 0.0
+        assert worst["intensity" + label] <= tol
+    # escaped rays end far from the horizon, where H is well conditioned: 5%.
+    # Captured rays end at r ~ r_h (1 + 1e-3), where p_r ~ 1/(r - r_h) turns
+    # relative state noise of ~1e-13 into ~1e-8 of H: agreement within 2x.
+    esc = ok & (ref["code"] == 0) & ~(diverged & (rel_diverged is not None))
+    oth = ok & ~esc
+    dh = np.abs(got["h_max"][esc] - ref["h_max"][esc])
+    lim = h_abs + h_rel * np.abs(ref["h_max"][esc])
+    worst["h_max_excess_escaped"] = float((dh / lim).max()) if dh.size else 0.0
+    g2, r2 = got["h_max"][oth], ref["h_max"][oth]
+    ratio = (np.maximum(g2, r2) + h_abs) / (np.minimum(g2, r2) + h_abs)
+    worst["h_max_ratio_other"] = float(ratio.max()) if ratio.size else 1.0
+    assert np.all(dh <= lim), "h_max (escaped) differs by %.3e" % dh.max()
+    assert np.all(ratio <= 2.0), "h_max (captured) differs by a factor %.2f" % ratio.max()
+    same_steps = float(np.mean((got["steps"] == ref["steps"]) & (got["rejects"] == ref["rejects"])))
+    worst["same_step_counts"] = same_steps
+    assert same_steps >= min_same_steps, same_steps
+    worst["band_pixels"] = len(band)
+    worst["n"] = n
+    if report is not None:
+        report.update(worst)
+    return worst
