@@ -151,7 +151,8 @@ def test_table_metric(T, orc):
     # Hermite interpolant (kinks at cell edges) such a ray then differs by the
     # interpolant-limited global error (~1e-8): rays with identical step counts
     # must still agree to 1e-9.
-    rep = parity.compare(orc, sc, got, ref, np.arange(sc.npix), min_same_steps=0.95, rel_diverged=1e-7)
+    rep = parity.compare(orc, sc, got, ref, np.arange(sc.npix), min_same_steps=0.95, rel_diverged=1e-7,
+                         h_ratio_only=True)
     print("table 48^2:", rep)
     # against the closed-form Kerr trace of the same scene: interpolation error only
     ana = run(T, sc.replace(metric_kind=0, table=None))
