@@ -188,6 +188,30 @@ typedef struct {
 int tartarus_trace_batch(const tt_image *images, int n, const tt_solver *solver,
                          const tt_tune *tune, int *status, void *cuda_stream);
 
+/* tartarus_trace_batch without any allocation (the paper has no counterpart;
+ * this is an interface for embedding).  For callers that must not allocate
+ * device memory once they are running -- for example an application that
+ * reserves its whole GPU memory budget at start-up and hands out all buffers
+ * itself, where a driver allocation from a library could exceed or fragment
+ * that budget.  tartarus_trace and tartarus_trace_batch allocate a small
+ * counter buffer on their first call on a device; this entry point instead
+ * uses a fixed 4 KiB array of work-queue counters compiled into the library
+ * (present on every device that loads it, until the process exits).
+ * Arguments, outputs and results are those of tartarus_trace_batch; the
+ * caller still owns every output buffer.  Limits and rules:
+ *   - at most 1024 images per call (16 counters, one per launch of up to 64
+ *     images); larger n returns TT_EINVAL before anything is launched;
+ *   - the first call on a device looks up the array's device address (a
+ *     runtime symbol query, no allocation) with that device current; make
+ *     that first call before any stream capture;
+ *   - every call shares the same counters and zeroes the ones it uses on its
+ *     stream before each launch, so two calls whose work overlaps on the GPU
+ *     (different streams, or different host threads) race on them: serialise
+ *     such calls, e.g. by issuing them on one stream.
+ * No cudaMalloc, cudaFree or other allocating routine is called. */
+int tartarus_trace_batch_noalloc(const tt_image *images, int n, const tt_solver *solver,
+                                 const tt_tune *tune, int *status, void *cuda_stream);
+
 /* Copy a metric table to the device (paper: numerically generated metrics).
  * host_nodes holds nth * nr * 20 doubles: node (j, k) at [(j nr + k) 20], with
  * r_k = r_min (r_max / r_min)^(k/(nr-1)) and theta_j = pi j / (nth-1); for each

@@ -276,9 +276,98 @@ int enqueue(const std::vector<tt::ImageDesc>& descs, const tt_solver* sol, const
     return TT_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Fixed device scratch for tartarus_trace_batch_noalloc.
+//
+// The tracer's only scratch is one 64-bit work-queue counter per launch (a
+// launch covers up to kMaxImagesPerLaunch images).  For callers that may not
+// allocate, those counters live in this file-scope array instead of the
+// lazily allocated ring above: kNoAllocSlots counters, one 256-byte line each
+// (4 KiB in all), present on every device that loads the library until the
+// process exits.  A call needs ceil(n / 64) counters, so it takes at most
+// kNoAllocSlots * 64 = 1024 images.  Host code must not pass the symbol
+// itself to a kernel (on the host it names a stand-in, not device memory):
+// its device address is looked up once per device and cached.
+// ---------------------------------------------------------------------------
+constexpr int kNoAllocSlots = 16;
+constexpr int kNoAllocMaxImages = kNoAllocSlots * tt::kMaxImagesPerLaunch;
+static __device__ __align__(256) unsigned long long tt_noalloc_queue[kNoAllocSlots * 32];
+unsigned long long* g_noalloc_addr[kMaxDevices] = {};
+std::mutex g_noalloc_mu;
+
+// Device address of the fixed scratch on the current device (looked up on the
+// first call on that device, with that device current).
+int noalloc_scratch(unsigned long long** out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return TT_ECUDA;
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, tt_noalloc_queue) != cudaSuccess || !p) return TT_ECUDA;
+        g_noalloc_addr[dev] = static_cast<unsigned long long*>(p);
+    }
+    *out = g_noalloc_addr[dev];
+    return TT_OK;
+}
+
 }  // namespace
 
 extern "C" {
+
+int tartarus_trace_batch_noalloc(const tt_image* images, int n, const tt_solver* solver, const tt_tune* tune,
+                                 int* status, void* cuda_stream) {
+    if (n < 0 || (n > 0 && !images)) return TT_EINVAL;
+    if (n > kNoAllocMaxImages) return TT_EINVAL;           // more counters than the fixed scratch holds
+    int rc = check_solver(solver);
+    if (rc) return rc;
+    rc = check_shape(tune);
+    if (rc) return rc;
+    unsigned long long* scratch = nullptr;
+    rc = noalloc_scratch(&scratch);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const tt::SolverDesc sd = make_solver(solver);
+    const tt::LaunchShape shape = make_shape(tune);
+    int worst = TT_OK;
+    int slot = 0;
+    tt::ImageDesc ds[tt::kMaxImagesPerLaunch];
+    int nd = 0;
+    long long total = 0;
+    int n_table = 0;
+    // validate and launch chunk by chunk (fixed-size host arrays, no heap)
+    for (int i = 0; i <= n; ++i) {
+        if (i < n) {
+            tt::ImageDesc d;
+            const tt_image& im = images[i];
+            int r = make_desc(&im.metric, &im.obs, &im.cam, solver, &im.disk, &im.out, &d);
+            if (status) status[i] = r;
+            if (r) {
+                worst = r;
+                continue;
+            }
+            if (d.pix_count == 0) continue;
+            d.ray_begin = total;
+            total += d.pix_count;
+            n_table += d.kind == TT_METRIC_TABLE;
+            ds[nd++] = d;
+        }
+        if ((nd == tt::kMaxImagesPerLaunch || i == n) && nd > 0) {
+            unsigned long long* q = scratch + (size_t)slot * 32;
+            ++slot;
+            const int metric_mode = n_table == 0 ? 0 : (n_table == nd ? 1 : 2);
+            // the array keeps the previous call's counts: zero this launch's counter first
+            cudaError_t e = cudaMemsetAsync(q, 0, sizeof(unsigned long long), st);
+            if (e == cudaSuccess) e = tt::launch_trace(ds, nd, total, metric_mode, sd, shape, q, st);
+            if (e != cudaSuccess) return TT_ECUDA;
+            g_launches.fetch_add(1);
+            nd = 0;
+            total = 0;
+            n_table = 0;
+        }
+    }
+    return worst;
+}
+
 
 int tartarus_trace(const tt_metric* metric, const tt_observer* obs, const tt_camera* cam, const tt_solver* solver,
                    const tt_disk* disk, const tt_outputs* out, const tt_tune* tune, void* cuda_stream) {

@@ -21,7 +21,8 @@ CODE_ESCAPED, CODE_CAPTURED, CODE_MAXSTEPS, CODE_UNDERFLOW, CODE_NONFINITE, CODE
 MAX_CROSSINGS = 3
 TABLE_NF = 20
 
-EXPORTS = ["tartarus_trace", "tartarus_trace_host", "tartarus_trace_batch", "tartarus_table_create",
+EXPORTS = ["tartarus_trace", "tartarus_trace_host", "tartarus_trace_batch", "tartarus_trace_batch_noalloc",
+           "tartarus_table_create",
            "tartarus_table_destroy", "tartarus_error_string", "tartarus_launch_count", "tartarus_version"]
 
 
@@ -100,6 +101,9 @@ def lib():
             L.tartarus_trace_host.restype = C.c_int
             L.tartarus_trace_batch.argtypes = [P(TTImage), C.c_int, P(TTSolver), P(TTTune), P(C.c_int), C.c_void_p]
             L.tartarus_trace_batch.restype = C.c_int
+            L.tartarus_trace_batch_noalloc.argtypes = [P(TTImage), C.c_int, P(TTSolver), P(TTTune), P(C.c_int),
+                                                       C.c_void_p]
+            L.tartarus_trace_batch_noalloc.restype = C.c_int
             L.tartarus_table_create.argtypes = [P(C.c_double), C.c_int, C.c_int, C.c_double, C.c_double,
                                                 P(C.c_void_p)]
             L.tartarus_table_create.restype = C.c_int
@@ -323,6 +327,33 @@ def trace_batch(scenes: Sequence[Scene], outs=None, stream=None, tune=None,
         status_out[:] = list(status)[:n]
     if st != TT_OK and status_out is None:
         _check(st, "tartarus_trace_batch")
+    return outs
+
+
+def trace_batch_noalloc(scenes: Sequence[Scene], outs, stream=None, tune=None,
+                        tables: Optional[Sequence[Optional[Table]]] = None,
+                        status_out: Optional[List[int]] = None):
+    """tartarus_trace_batch_noalloc: like trace_batch, but the library allocates
+    nothing (its work-queue counters sit in a fixed array inside the library).
+    The caller supplies the output tensors; at most 1024 images per call, and
+    calls that overlap on the GPU race on the shared counters."""
+    n = len(scenes)
+    imgs = (TTImage * max(n, 1))()
+    for i, s in enumerate(scenes):
+        tb = tables[i] if tables is not None else None
+        imgs[i].metric = _metric(s, tb)
+        imgs[i].obs = TTObserver(s.r_obs, s.theta_obs)
+        imgs[i].cam = _camera(s, 0, 0)
+        imgs[i].disk = _disk(s)
+        imgs[i].out = _out_struct(outs[i])
+    status = (C.c_int * max(n, 1))()
+    st = lib().tartarus_trace_batch_noalloc(imgs, n, C.byref(solver_struct(scenes[0])),
+                                            C.byref(_tune(tune)) if tune is not None else None, status,
+                                            _stream_ptr(stream))
+    if status_out is not None:
+        status_out[:] = list(status)[:n]
+    if st != TT_OK and status_out is None:
+        _check(st, "tartarus_trace_batch_noalloc")
     return outs
 
 
