@@ -49,6 +49,9 @@ def parse():
     p.add_argument("--n", type=int, default=1024, help="camera resolution (default: the 1024^2 workload)")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="oracle sample budget per measurement")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--precision", default="fp64", choices=["fp64", "mixed", "mixed_pair"],
+                   help="path of the main measurement (default: the FP64 headline)")
+    p.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision objects")
     return p.parse_args()
 
 
@@ -59,9 +62,35 @@ def dist_env():
     return rank, world, local
 
 
-def workload(n):
+PRECISIONS = {"fp64": 0, "mixed": 1, "mixed_pair": 2}
+
+
+def workload(n, precision="fp64"):
     from paper_2609_08989_gb300 import scenes
-    return scenes.kerr_disk(n)
+    if precision == "fp64":
+        return scenes.kerr_disk(n)
+    return scenes.kerr_disk_mixed(n).replace(precision=PRECISIONS[precision])
+
+
+def time_variant(T, sc, steps, warmup, flush, tune=None):
+    """Device time per image of one scene (CUDA events, L2 flushed between images)."""
+    import torch
+    out = T.alloc_outputs(sc.npix)
+    stream = torch.cuda.current_stream()
+    for k in range(max(warmup, 1)):
+        flush.fill_(k & 0xFF)
+        T.trace(sc, out=out, tune=tune)
+    torch.cuda.synchronize()
+    ms = []
+    for k in range(steps):
+        flush.fill_(k & 0xFF)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        T.trace(sc, out=out, stream=stream, tune=tune)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    return sum(ms) / len(ms), out
 
 
 def config_dict(sc, world):
@@ -188,7 +217,7 @@ def run_tartarus(args):
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    sc = workload(args.n)
+    sc = workload(args.n, args.precision)
     T.lib()
     out = T.alloc_outputs(sc.npix)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
@@ -247,6 +276,23 @@ def run_tartarus(args):
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
     e2e_value = world * sc.npix * args.steps / float(tt.item())
 
+    mixed = {}
+    if not args.no_mixed and args.precision == "fp64":
+        # the mixed-precision paths on the same Kerr disk scene at 2048^2, each at
+        # the tolerance that keeps |H| <= 1e-6 on escaped rays
+        for name in ("mixed", "mixed_pair"):
+            msc = workload(2 * args.n, name)
+            ms, mout = time_variant(T, msc, max(2, args.steps // 2), 1, flush)
+            h = mout["h_max"].cpu().numpy()
+            code = mout["code"].cpu().numpy()
+            esc = code == 0
+            mixed[name] = {"value": msc.npix / (ms / 1e3), "unit": UNIT, "ms_per_image": ms,
+                           "workload": msc.name, "rtol": msc.rtol,
+                           "accumulation": "fp64" if name == "mixed" else "compensated fp32 pair",
+                           "h_max_escaped": float(h[esc].max()) if esc.any() else None,
+                           "h_max_escaped_p99": float(np.percentile(h[esc], 99)) if esc.any() else None,
+                           "h_max_captured": float(h[~esc].max()) if (~esc).any() else None,
+                           "rk_step_attempts_per_image": int(mout["steps"].sum().item() + mout["rejects"].sum().item())}
     if rank == 0:
         flops = FLOPS_PER_STEP * step_attempts
         achieved = flops / (mean_kern / 1e3) / 1e12
@@ -267,6 +313,10 @@ def run_tartarus(args):
             "gpu_launches": launches,
             "clocks": clk,
         }
+        if args.precision != "fp64":
+            line["dtype"] = "f32 stages / f64 state" if args.precision == "mixed" else "f32 stages / f32-pair state"
+            line["roofline"] = None          # the FP64 flop count does not describe the mixed step
+        line.update(mixed)
         if not args.no_cpu_baseline:
             v, rays, cores, tsec = time_oracle(sc, args.cpu_seconds)
             line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",

@@ -64,6 +64,7 @@ extern "C" {
 #define TT_DP54          0   /* Dormand-Prince 5(4) (paper Sec. 3.2)   */
 #define TT_FP64          0   /* all arithmetic in binary64             */
 #define TT_MIXED         1   /* FP32 stages, FP64 state accumulation   */
+#define TT_MIXED_PAIR    2   /* FP32 stages, compensated FP32-pair state accumulation (~48 bits) */
 #define TT_REFINE_HENON   0  /* exact step onto theta = pi/2 (default) */
 #define TT_REFINE_HERMITE 1  /* paper's cubic-Hermite bisection        */
 
@@ -96,7 +97,14 @@ typedef struct {
  * max_steps >= 1 caps accepted + rejected steps.  Captured when
  * r < r_h (1 + horizon_eps), escaped when r > escape_factor * r_obs
  * (escape_factor > 1).  fp64_radius_factor (mixed only): steps that start at
- * r < fp64_radius_factor * r_h run in FP64 (<= 0 selects 1.5). */
+ * r < fp64_radius_factor * r_h run in FP64 (0 selects 1.5, negative: none);
+ * so do steps that start with sin(theta) < fp64_pole_sin (0 selects 0.1,
+ * negative: none), where L^2 / sin^2(theta) makes FP32 lose the constraint.
+ * TT_MIXED and TT_MIXED_PAIR are available for the closed-form Kerr metric;
+ * with a table they return TT_EUNSUPPORTED.  On the mixed paths h_max is the
+ * largest |H| evaluated in FP64: at the start, at every FP64 step, at the
+ * start of every step with a disk crossing, every monitor_period warp
+ * iterations and at the end. */
 typedef struct {
     int method;                 /* TT_DP54 */
     int precision;              /* TT_FP64 or TT_MIXED */
@@ -105,6 +113,7 @@ typedef struct {
     double horizon_eps, escape_factor;
     int refine;                 /* TT_REFINE_HENON or TT_REFINE_HERMITE */
     double fp64_radius_factor;
+    double fp64_pole_sin;
 } tt_solver;
 
 /* Thin disk in the equatorial plane (paper Sec. 2.3).  r_in <= 0 selects the
@@ -142,16 +151,29 @@ typedef struct {
     int32_t *rejects;
 } tt_outputs;
 
-/* Launch shape; NULL or zero fields select the tuned defaults.
- *   block        threads per block (multiple of 32, 32..1024)
- *   reg_variant  0: default register cap, 1..4: tighter caps (64/80/96/128 regs)
- *   refill       refill idle lanes when at least this many lanes of a warp are idle (1..32)
- *   blocks_per_sm  persistent blocks per SM (0: from occupancy) */
+/* Launch shape of the persistent kernel; NULL or zero fields select defaults.
+ *   block           threads per block: 128 (default) or 256
+ *   reg_variant     register-cap variant; only 0 (the compiler's choice) is built
+ *   refill          flush finished rays and refill lanes once at least this many
+ *                   lanes of a warp are done or idle (1..32, default 8)
+ *   blocks_per_sm   persistent blocks per SM (0: as many as fit)
+ *   crossing_batch  refine disk crossings once this many lanes of a warp have
+ *                   one pending (1..32, default 8)
+ *   fp64_batch      mixed paths: run the FP64 near-horizon steps once this many
+ *                   lanes need one (1..32, default 8)
+ *   monitor_period  mixed paths: evaluate |H| in FP64 every this many warp
+ *                   iterations (default 32)
+ *   fp64_wait       mixed paths: lanes waiting for an FP64 step get one after at
+ *                   most this many warp iterations (default 64) */
 typedef struct {
     int block;
     int reg_variant;
     int refill;
     int blocks_per_sm;
+    int crossing_batch;
+    int fp64_batch;
+    int monitor_period;
+    int fp64_wait;
 } tt_tune;
 
 /* Trace one camera (paper Sec. 3.1 execution flow, steps 1-6): every pixel of

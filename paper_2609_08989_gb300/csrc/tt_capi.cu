@@ -57,15 +57,14 @@ int check_metric(const tt_metric* m) {
 int check_solver(const tt_solver* s) {
     if (!s) return TT_EINVAL;
     if (s->method != TT_DP54) return TT_EUNSUPPORTED;
-    if (s->precision != TT_FP64 && s->precision != TT_MIXED) return TT_EINVAL;
-    if (s->precision == TT_MIXED) return TT_EUNSUPPORTED;
+    if (s->precision != TT_FP64 && s->precision != TT_MIXED && s->precision != TT_MIXED_PAIR) return TT_EINVAL;
     if (!is_finite(s->rtol) || !is_finite(s->atol) || !(s->rtol > 0.0) || !(s->atol > 0.0)) return TT_EINVAL;
     if (!is_finite(s->h0) || !is_finite(s->h_min)) return TT_EINVAL;
     if (s->max_steps < 1) return TT_EINVAL;
     if (!is_finite(s->horizon_eps) || s->horizon_eps < 0.0) return TT_EINVAL;
     if (!is_finite(s->escape_factor) || !(s->escape_factor > 1.0)) return TT_EINVAL;
     if (s->refine != TT_REFINE_HENON && s->refine != TT_REFINE_HERMITE) return TT_EINVAL;
-    if (!is_finite(s->fp64_radius_factor)) return TT_EINVAL;
+    if (!is_finite(s->fp64_radius_factor) || !is_finite(s->fp64_pole_sin)) return TT_EINVAL;
     return TT_OK;
 }
 
@@ -114,6 +113,7 @@ int make_desc(const tt_metric* m, const tt_observer* obs, const tt_camera* cam, 
     d->M = m->M;
     d->a = m->a;
     double r_h;
+    if (m->kind == TT_METRIC_TABLE && sol->precision != TT_FP64) return TT_EUNSUPPORTED;
     if (m->kind == TT_METRIC_TABLE) {
         const tt_table* t = m->table;
         d->table = t->d_nodes;
@@ -125,10 +125,30 @@ int make_desc(const tt_metric* m, const tt_observer* obs, const tt_camera* cam, 
         r_h = t->r_min;
     } else {
         r_h = kerr_rplus(m->M, m->a);
+        d->r_plus = r_h;
+        d->r_minus = m->M - std::sqrt(m->M * m->M - m->a * m->a);
+        // the observer's metric and ZAMO tetrad are the same for every pixel
+        const double M = m->M, a = m->a, r = obs->r_obs;
+        const double s = std::sin(obs->theta_obs), c = std::cos(obs->theta_obs), s2 = s * s;
+        const double Sig = r * r + a * a * c * c, Del = r * r - 2.0 * M * r + a * a;
+        const double g[5] = {-(1.0 - 2.0 * M * r / Sig), -2.0 * M * a * r * s2 / Sig, Sig / Del, Sig,
+                             (r * r + a * a + 2.0 * M * a * a * r * s2 / Sig) * s2};
+        const double omega = -g[1] / g[4];
+        const double N = std::sqrt(-g[0] + omega * omega * g[4]);
+        for (int i = 0; i < 5; ++i) d->obs_g[i] = g[i];
+        d->obs_omN = omega / N;
+        d->obs_iN = 1.0 / N;
+        d->obs_ir = 1.0 / std::sqrt(g[2]);
+        d->obs_ith = 1.0 / std::sqrt(g[3]);
+        d->obs_iph = 1.0 / std::sqrt(g[4]);
+        d->obs_ready = 1;
     }
     d->r_capture = r_h * (1.0 + sol->horizon_eps);
     d->r_escape = sol->escape_factor * obs->r_obs;
-    d->r_fp64 = (sol->fp64_radius_factor > 0.0 ? sol->fp64_radius_factor : 1.5) * r_h;
+    // mixed path: steps starting below r_fp64 run in FP64 (factor 0 -> 1.5, negative -> never)
+    d->r_fp64 = sol->fp64_radius_factor < 0.0 ? 0.0 : (sol->fp64_radius_factor > 0.0 ? sol->fp64_radius_factor : 1.5) * r_h;
+    // ... and within asin(fp64_pole_sin) of the axis (0 -> 0.1, negative -> never)
+    d->th_pole = sol->fp64_pole_sin < 0.0 ? 0.0 : std::asin(std::min(1.0, sol->fp64_pole_sin > 0.0 ? sol->fp64_pole_sin : 0.1));
     d->disk = disk->enabled ? 1 : 0;
     d->max_cross = disk->enabled ? disk->max_crossings : 0;
     d->doppler = disk->doppler ? 1 : 0;
@@ -187,12 +207,16 @@ tt::SolverDesc make_solver(const tt_solver* s) {
 }
 
 tt::LaunchShape make_shape(const tt_tune* t) {
-    tt::LaunchShape s{128, 0, 8, 0};
+    tt::LaunchShape s{0, 0, 0, 0, 0, 0, 0, 0};       // zeros: the kernel's defaults
     if (t) {
         if (t->block > 0) s.block = t->block;
         if (t->reg_variant > 0) s.reg_variant = t->reg_variant;
         if (t->refill > 0) s.refill = t->refill;
         if (t->blocks_per_sm > 0) s.blocks_per_sm = t->blocks_per_sm;
+        if (t->crossing_batch > 0) s.crossing_batch = t->crossing_batch;
+        if (t->fp64_batch > 0) s.fp64_batch = t->fp64_batch;
+        if (t->monitor_period > 0) s.monitor_period = t->monitor_period;
+        if (t->fp64_wait > 0) s.fp64_wait = t->fp64_wait;
     }
     return s;
 }
@@ -200,9 +224,14 @@ tt::LaunchShape make_shape(const tt_tune* t) {
 int check_shape(const tt_tune* t) {
     if (!t) return TT_OK;
     if (t->block != 0 && t->block != 128 && t->block != 256) return TT_EUNSUPPORTED;
-    if (t->reg_variant < 0 || t->reg_variant > 4) return TT_EINVAL;
+    // built variants: 128 or 256 threads (FP64, closed-form Kerr), 128 (FP64 tables),
+    // 256 (mixed paths)
+    if (t->reg_variant != 0) return TT_EUNSUPPORTED;
     if (t->refill < 0 || t->refill > 32) return TT_EINVAL;
     if (t->blocks_per_sm < 0) return TT_EINVAL;
+    if (t->crossing_batch < 0 || t->crossing_batch > 32) return TT_EINVAL;
+    if (t->fp64_batch < 0 || t->fp64_batch > 32) return TT_EINVAL;
+    if (t->monitor_period < 0 || t->fp64_wait < 0) return TT_EINVAL;
     return TT_OK;
 }
 

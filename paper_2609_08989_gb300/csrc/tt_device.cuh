@@ -36,6 +36,7 @@ struct RayConst {
     double pph2;          // p_phi^2
     double a2pt2;         // a^2 p_t^2
     double c0;            // 2 a p_t p_phi
+    double pt4;           // 4 p_t
 };
 
 __device__ __forceinline__ RayConst make_ray_const(double a, double pt, double pph) {
@@ -46,7 +47,23 @@ __device__ __forceinline__ RayConst make_ray_const(double a, double pt, double p
     R.pph2 = pph * pph;
     R.a2pt2 = a * a * pt * pt;
     R.c0 = 2.0 * a * pt * pph;
+    R.pt4 = 4.0 * pt;
     return R;
+}
+
+// Per-spacetime constants of the closed-form Kerr flow.
+struct KerrK {
+    double M, a, a2, twoM, fourA2;
+};
+
+__device__ __forceinline__ KerrK make_kerr(double M, double a) {
+    KerrK k;
+    k.M = M;
+    k.a = a;
+    k.a2 = a * a;
+    k.twoM = 2.0 * M;
+    k.fourA2 = 4.0 * a * a;
+    return k;
 }
 
 struct State {
@@ -64,17 +81,16 @@ struct State {
 // off the constraint surface).  One reciprocal serves 1/Sigma, 1/Delta and
 // 1/sin^2.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void kerr_flow64(double M, double a, const RayConst& R, const State& y,
+__device__ __forceinline__ void kerr_flow64(const KerrK& k, const RayConst& R, const State& y,
                                             State& f, double& H) {
     double s, c;
     sincos(y.th, &s, &c);
-    const double a2 = a * a;
     const double r = y.r;
     double s2 = s * s, c2 = c * c, sc = s * c;
     double r2 = r * r;
-    double Sig = fma(a2, c2, r2);
-    double Del = fma(r, r - 2.0 * M, a2);
-    double A = fma(r2 + a2, R.pt, R.apph);
+    double Sig = fma(k.a2, c2, r2);
+    double Del = fma(r, r - k.twoM, k.a2);
+    double A = fma(r2 + k.a2, R.pt, R.apph);
     double SD = Sig * Del;
     double inv = rcp64(SD * s2);
     double iS = inv * (Del * s2);
@@ -87,14 +103,100 @@ __device__ __forceinline__ void kerr_flow64(double M, double a, const RayConst& 
     K = fma(y.pth, y.pth, K);
     K = fma(Del, pr2, K);
     K = fma(-A, AiD, K);
-    H = 0.5 * K * iS;
-    double dKr = fma(2.0 * (r - M), fma(AiD, AiD, pr2), -4.0 * r * R.pt * AiD);
-    double dKt = 2.0 * sc * fma(-R.pph2, u * u, R.a2pt2);
     double hiS = 0.5 * iS;
-    f.r = Del * iS * y.pr;
+    H = K * hiS;
+    double Dr = fma(2.0, r, -k.twoM);                          // dDelta/dr
+    double dKr = fma(Dr, fma(AiD, AiD, pr2), -(r * R.pt4) * AiD);
+    double dKt = (2.0 * sc) * fma(-R.pph2, u * u, R.a2pt2);
+    f.r = (Del * iS) * y.pr;
     f.th = y.pth * iS;
     f.pr = fma(4.0 * r, H, -dKr) * hiS;
-    f.pth = -fma(4.0 * a2 * sc, H, dKt) * hiS;
+    f.pth = -fma(k.fourA2 * sc, H, dKt) * hiS;
+}
+
+// ---------------------------------------------------------------------------
+// FP32 Kerr flow for the mixed-precision stages.  Same Hamiltonian, arranged
+// for single precision:
+//  * Delta = (r - r_+)(r - r_-) from dr = r - r_+, which the caller forms from
+//    the high-precision state, so the flow stays relatively accurate down to
+//    the horizon event;
+//  * the radial force uses the exact (off-shell) identity
+//      dK/dr - 4 r H = [K C - Delta' T + 2 A Q / Delta] / Delta,
+//      C = (2M (r^2 - a^2 cos^2) - 2 r a^2 sin^2) / Sigma,
+//      T = p_th^2 + (p_phi + a p_t sin^2)^2 / sin^2,
+//      Q = 2M (r^2 - a^2) p_t + (2r - 2M) a p_phi,
+//    in which the O(r^3) terms that cancel in dK/dr are already cancelled
+//    analytically; in the direct form FP32 loses ~r^2/b^2 of its precision
+//    far from the hole (10^4 at r = 1000), which shows up as drift of H.
+// ---------------------------------------------------------------------------
+struct RayConstF {
+    float pt, pph, apph, pph2, a2pt2, c0, twoMpt;
+};
+
+__device__ __forceinline__ RayConstF to_float(const RayConst& R, double M) {
+    RayConstF F;
+    F.pt = (float)R.pt;
+    F.pph = (float)R.pph;
+    F.apph = (float)R.apph;
+    F.pph2 = (float)R.pph2;
+    F.a2pt2 = (float)R.a2pt2;
+    F.c0 = (float)R.c0;
+    F.twoMpt = (float)(2.0 * M * R.pt);
+    return F;
+}
+
+struct StateF {
+    float r, th, pr, pth;
+};
+
+// M, a^2 and r_+ - r_- in FP32; dr = r - r_+.
+__device__ __forceinline__ void kerr_flow32(float M, float a2, float rpm, const RayConstF& R, const StateF& y,
+                                            float dr, StateF& f, float& H) {
+    float s, c;
+    sincosf(y.th, &s, &c);
+    const float r = y.r;
+    float s2 = s * s, c2 = c * c, sc = s * c;
+    float r2 = r * r;
+    float Sig = fmaf(a2, c2, r2);
+    float Del = dr * (dr + rpm);
+    float A = fmaf(r2 + a2, R.pt, R.apph);
+    float SD = Sig * Del;
+    float inv = __frcp_rn(SD * s2);
+    float iS = inv * (Del * s2);
+    float iD = inv * (Sig * s2);
+    float u = inv * SD;
+    float pr2 = y.pr * y.pr;
+    float AiD = A * iD;
+    float T = fmaf(y.pth, y.pth, fmaf(R.pph2, u, fmaf(R.a2pt2, s2, R.c0)));
+    float K = fmaf(-A, AiD, fmaf(Del, pr2, T));
+    float hiS = 0.5f * iS;
+    H = K * hiS;
+    float twoM = 2.0f * M;
+    float Dr = fmaf(2.0f, r, -twoM);
+    float C = fmaf(twoM, fmaf(-a2, c2, r2), -2.0f * r * a2 * s2) * iS;
+    float Q = fmaf(R.twoMpt, r2 - a2, Dr * R.apph);
+    float G = fmaf(K, C, fmaf(-Dr, T, 2.0f * AiD * Q));
+    float dKt = 2.0f * sc * fmaf(-R.pph2, u * u, R.a2pt2);
+    f.r = Del * iS * y.pr;
+    f.th = y.pth * iS;
+    f.pr = -G * iD * hiS;
+    f.pth = -fmaf(4.0f * a2 * sc, H, dKt) * hiS;
+}
+
+// H alone (no derivatives), FP64: the mixed paths' constraint monitor.
+__device__ __forceinline__ double kerr_h64(const KerrK& k, const RayConst& R, const State& y) {
+    double s, c;
+    sincos(y.th, &s, &c);
+    const double r = y.r;
+    double s2 = s * s, r2 = r * r;
+    double Sig = fma(k.a2, c * c, r2);
+    double Del = fma(r, r - k.twoM, k.a2);
+    double A = fma(r2 + k.a2, R.pt, R.apph);
+    double SD = Sig * Del;
+    double inv = rcp64(SD * s2);
+    double T = fma(y.pth, y.pth, fma(R.pph2, inv * SD, fma(R.a2pt2, s2, R.c0)));
+    double K = fma(-A, A * (inv * Sig * s2), fma(Del, y.pr * y.pr, T));
+    return 0.5 * K * (inv * Del * s2);
 }
 
 // Kerr g_tt, g_tphi, g_rr, g_thth, g_phiphi (Boyer-Lindquist).
@@ -209,9 +311,9 @@ __device__ __forceinline__ void table_lower64(const ImageDesc& d, double r, doub
 
 // METRIC: 0 closed-form Kerr, 1 table, 2 chosen per image at run time.
 template <int METRIC>
-__device__ __forceinline__ void flow64(const ImageDesc& d, double M, double a, const RayConst& R,
+__device__ __forceinline__ void flow64(const ImageDesc& d, const KerrK& k, const RayConst& R,
                                        const State& y, State& f, double& H) {
-    if (METRIC == 0 || (METRIC == 2 && d.kind == 0)) kerr_flow64(M, a, R, y, f, H);
+    if (METRIC == 0 || (METRIC == 2 && d.kind == 0)) kerr_flow64(k, R, y, f, H);
     else table_flow64(d, R, y, f, H);
 }
 

@@ -20,6 +20,12 @@ struct ImageDesc {
     double alpha_min, dalpha, beta_min, dbeta;
     // observer
     double r_obs, theta_obs;
+    // ZAMO tetrad at the observer, resolved on the host for the closed-form
+    // metric (obs_ready = 1): g_tt, g_tphi, g_rr, g_thth, g_phiphi, omega/N,
+    // 1/N, 1/sqrt(g_rr), 1/sqrt(g_thth), 1/sqrt(g_phiphi)
+    int obs_ready;
+    double obs_g[5];
+    double obs_omN, obs_iN, obs_ir, obs_ith, obs_iph;
     // metric
     int kind;                     // 0 Kerr, 1 table
     double M, a;
@@ -30,6 +36,8 @@ struct ImageDesc {
     double r_capture;             // r_h (1 + horizon_eps)
     double r_escape;              // escape_factor * r_obs
     double r_fp64;                // mixed path: FP64 steps below this radius
+    double th_pole;               // mixed path: FP64 steps within this angle of the axis
+    double r_plus, r_minus;       // Kerr horizons (mixed path: Delta = (r - r_+)(r - r_-))
     // disk
     int disk, max_cross, doppler;
     double r_in, r_out, mdot;
@@ -55,7 +63,7 @@ struct SolverDesc {
     double rtol, atol, h0, h_min;
     long long max_steps;
     int refine;                   // 0 Henon, 1 Hermite
-    int precision;                // 0 FP64, 1 mixed
+    int precision;                // 0 FP64, 1 mixed (FP64 state), 2 mixed (FP32-pair state)
 };
 
 struct LaunchShape {
@@ -63,6 +71,19 @@ struct LaunchShape {
     int reg_variant;
     int refill;
     int blocks_per_sm;
+    int crossing_batch;
+    int fp64_batch;
+    int monitor_period;
+    int fp64_wait;
+};
+
+// Warp-phase thresholds of the persistent loop (see tt_kernel.cu).
+struct TuneParams {
+    int refill;           // refill when at least this many lanes are done or idle
+    int crossing_batch;   // refine crossings once this many lanes have one pending
+    int fp64_batch;       // mixed: run FP64 steps once this many lanes need one
+    int monitor_period;   // mixed: FP64 |H| check every this many iterations
+    int fp64_wait;        // mixed: FP64 steps run after this many iterations of waiting
 };
 
 // Images handed to one launch by value (kernel parameters, no host-to-device
@@ -73,7 +94,7 @@ template <int N>
 struct LaunchParams {
     SolverDesc sol;
     int n_desc;
-    int refill;
+    TuneParams tune;
     long long total;                 // rays over all images
     unsigned long long* queue;       // zeroed 64-bit counter
     ImageDesc desc[N];

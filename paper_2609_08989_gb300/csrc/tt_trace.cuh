@@ -1,0 +1,824 @@
+// tt_trace.cuh -- device code of the persistent ray-tracing kernels (sm_103a).
+//
+// One ray per thread; warps pull rays from a shared queue (one atomicAdd per
+// warp refill).  On GB300 an FP64 instruction issues at 1/64 of the FP32 rate
+// and a warp pays for its inactive lanes, so per-ray FP64 work outside the
+// regular step (initial data, crossing refinement and emission, the final
+// record, the mixed path's FP64 steps and |H| checks) runs in warp-uniform
+// phases in which every lane that needs it takes part at once:
+//
+//   refill phase  : when >= `refill` lanes are done or idle (or none runs):
+//                   pending crossings are refined, finished rays are written,
+//                   idle lanes take new rays and build their initial data;
+//   FP64 steps    : FP64 path: every running lane.  Mixed path: lanes near the
+//                   horizon (r < r_fp64) or the axis (sin theta < the pole
+//                   threshold) wait until `fp64_batch` of them (or every
+//                   running lane) need an FP64 step, or they have waited
+//                   `fp64_wait` iterations;
+//   FP32 steps    : mixed path, every other running lane;
+//   crossings     : once >= `crossing_batch` lanes have a crossing pending;
+//   |H| check     : mixed path, every `monitor_period` iterations, in FP64.
+//
+// Every loop is bounded: a lane takes at most max_steps steps per ray and each
+// warp iteration either steps rays or consumes queue entries; nothing waits on
+// another thread.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "tt_device.cuh"
+#include "tt_internal.h"
+
+namespace tt {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// x^(-1/10) for the step-size factor: the SFU's single-precision power refined
+// by one Newton step of y^-10 = x, y <- y (1.1 - 0.1 x y^10), which squares the
+// relative error (~1e-7 -> ~1e-13).  Callers handle x < 1e-30 themselves.
+__device__ __forceinline__ double pow_m01(double x) {
+    double y = (double)__powf((float)x, -0.1f);
+    double y2 = y * y, y4 = y2 * y2, y10 = y4 * y4 * y2;
+    return y * fma(-0.1 * x, y10, 1.1);
+}
+
+// Step-size factor 0.9 err^(-1/5) from err^2 (large when err^2 is tiny or 0).
+__device__ __forceinline__ double step_factor(double err2) {
+    return (err2 < 1e-30) ? 1e30 : 0.9 * pow_m01(err2);
+}
+
+// ---------------------------------------------------------------------------
+// One Dormand-Prince step in FP64 (paper Sec. 3.2): returns the fifth-order
+// point yn, its flow kn (first-same-as-last) and H there, and the error vector.
+// ---------------------------------------------------------------------------
+template <int METRIC>
+__device__ __forceinline__ void dp5_step64(const ImageDesc& d, const KerrK& kk, const RayConst& R,
+                                           const State& y, const State& k1, double h, State& yn,
+                                           State& kn, double& Hn, State& err) {
+    using namespace dp;
+    State k2, k3, k4, k5, k6, ys;
+    double Hs;
+#define TT_STAGE(dst, expr_r, expr_t, expr_p, expr_q)                                \
+    ys.r = fma(h, (expr_r), y.r);                                                    \
+    ys.th = fma(h, (expr_t), y.th);                                                  \
+    ys.pr = fma(h, (expr_p), y.pr);                                                  \
+    ys.pth = fma(h, (expr_q), y.pth);                                                \
+    flow64<METRIC>(d, kk, R, ys, dst, Hs);
+#define TT_C2(f) (a21 * k1.f)
+#define TT_C3(f) fma(a32, k2.f, a31 * k1.f)
+#define TT_C4(f) fma(a43, k3.f, fma(a42, k2.f, a41 * k1.f))
+#define TT_C5(f) fma(a54, k4.f, fma(a53, k3.f, fma(a52, k2.f, a51 * k1.f)))
+#define TT_C6(f) fma(a65, k5.f, fma(a64, k4.f, fma(a63, k3.f, fma(a62, k2.f, a61 * k1.f))))
+#define TT_C7(f) fma(b6, k6.f, fma(b5, k5.f, fma(b4, k4.f, fma(b3, k3.f, b1 * k1.f))))
+    TT_STAGE(k2, TT_C2(r), TT_C2(th), TT_C2(pr), TT_C2(pth))
+    TT_STAGE(k3, TT_C3(r), TT_C3(th), TT_C3(pr), TT_C3(pth))
+    TT_STAGE(k4, TT_C4(r), TT_C4(th), TT_C4(pr), TT_C4(pth))
+    TT_STAGE(k5, TT_C5(r), TT_C5(th), TT_C5(pr), TT_C5(pth))
+    TT_STAGE(k6, TT_C6(r), TT_C6(th), TT_C6(pr), TT_C6(pth))
+    yn.r = fma(h, TT_C7(r), y.r);
+    yn.th = fma(h, TT_C7(th), y.th);
+    yn.pr = fma(h, TT_C7(pr), y.pr);
+    yn.pth = fma(h, TT_C7(pth), y.pth);
+    flow64<METRIC>(d, kk, R, yn, kn, Hn);
+#define TT_E(f) h * fma(e7, kn.f, fma(e6, k6.f, fma(e5, k5.f, fma(e4, k4.f, fma(e3, k3.f, e1 * k1.f)))))
+    err.r = TT_E(r);
+    err.th = TT_E(th);
+    err.pr = TT_E(pr);
+    err.pth = TT_E(pth);
+#undef TT_E
+#undef TT_STAGE
+#undef TT_C2
+#undef TT_C3
+#undef TT_C4
+#undef TT_C5
+#undef TT_C6
+#undef TT_C7
+}
+
+__device__ __forceinline__ double sq_ratio(double e, double y, double yn, double atol, double rtol) {
+    double sc = fma(rtol, fmax(fabs(y), fabs(yn)), atol);
+    double q = e * rcp64(sc);
+    return q * q;
+}
+
+// Mean-square error norm over (r, theta, p_r, p_theta).
+__device__ __forceinline__ double err_norm2(const State& y, const State& yn, const State& e,
+                                            double atol, double rtol) {
+    double s = sq_ratio(e.r, y.r, yn.r, atol, rtol);
+    s += sq_ratio(e.th, y.th, yn.th, atol, rtol);
+    s += sq_ratio(e.pr, y.pr, yn.pr, atol, rtol);
+    s += sq_ratio(e.pth, y.pth, yn.pth, atol, rtol);
+    return 0.25 * s;
+}
+
+// ---------------------------------------------------------------------------
+// Crossing refinement.
+// Henon's exact step: integrate dz/dtheta = f / (dtheta/dlambda) for
+// z = (r, p_r, p_th) from the start of the accepted step to theta = pi/2 with
+// Dormand-Prince in 2^m equal sub-steps, m = 0..6, taking the first m whose
+// largest sub-step error norm (over r, p_r, p_th) is <= 1.
+// ---------------------------------------------------------------------------
+template <int METRIC>
+__device__ __forceinline__ void theta_flow64(const ImageDesc& d, const KerrK& kk, const RayConst& R,
+                                             const State& y, State& g) {
+    State f;
+    double H;
+    flow64<METRIC>(d, kk, R, y, f, H);
+    double it = rcp64(f.th);
+    g.r = f.r * it;
+    g.th = 1.0;
+    g.pr = f.pr * it;
+    g.pth = f.pth * it;
+}
+
+template <int METRIC>
+__device__ double refine_henon64(const ImageDesc& d, const KerrK& kk, const RayConst& R,
+                                 const State& y0, const State& f0, double atol, double rtol) {
+    using namespace dp;
+    const double dth_all = kHalfPi - y0.th;
+    const double it0 = rcp64(f0.th);
+    State g0;
+    g0.r = f0.r * it0;
+    g0.pr = f0.pr * it0;
+    g0.pth = f0.pth * it0;
+    double r_out = y0.r;
+    for (int m = 0; m <= 6; ++m) {
+        const int nsub = 1 << m;
+        const double dl = dth_all / (double)nsub;
+        State z = y0, g = g0;
+        double worst = 0.0;
+        for (int q = 0; q < nsub; ++q) {
+            State k2, k3, k4, k5, k6, k7, zs;
+            const double th0 = z.th;
+#define TT_HS(dst, cc, er, ep, eq)                        \
+    zs.r = fma(dl, (er), z.r);                            \
+    zs.pr = fma(dl, (ep), z.pr);                          \
+    zs.pth = fma(dl, (eq), z.pth);                        \
+    zs.th = fma(dl, (cc), th0);                           \
+    theta_flow64<METRIC>(d, kk, R, zs, dst);
+#define TT_C2(f) (a21 * g.f)
+#define TT_C3(f) fma(a32, k2.f, a31 * g.f)
+#define TT_C4(f) fma(a43, k3.f, fma(a42, k2.f, a41 * g.f))
+#define TT_C5(f) fma(a54, k4.f, fma(a53, k3.f, fma(a52, k2.f, a51 * g.f)))
+#define TT_C6(f) fma(a65, k5.f, fma(a64, k4.f, fma(a63, k3.f, fma(a62, k2.f, a61 * g.f))))
+#define TT_C7(f) fma(b6, k6.f, fma(b5, k5.f, fma(b4, k4.f, fma(b3, k3.f, b1 * g.f))))
+            TT_HS(k2, c2, TT_C2(r), TT_C2(pr), TT_C2(pth))
+            TT_HS(k3, c3, TT_C3(r), TT_C3(pr), TT_C3(pth))
+            TT_HS(k4, c4, TT_C4(r), TT_C4(pr), TT_C4(pth))
+            TT_HS(k5, c5, TT_C5(r), TT_C5(pr), TT_C5(pth))
+            TT_HS(k6, 1.0, TT_C6(r), TT_C6(pr), TT_C6(pth))
+            State zn;
+            zn.r = fma(dl, TT_C7(r), z.r);
+            zn.pr = fma(dl, TT_C7(pr), z.pr);
+            zn.pth = fma(dl, TT_C7(pth), z.pth);
+            zn.th = th0 + dl;
+            theta_flow64<METRIC>(d, kk, R, zn, k7);
+#define TT_E(f) dl * fma(e7, k7.f, fma(e6, k6.f, fma(e5, k5.f, fma(e4, k4.f, fma(e3, k3.f, e1 * g.f)))))
+            double s = sq_ratio(TT_E(r), z.r, zn.r, atol, rtol);
+            s += sq_ratio(TT_E(pr), z.pr, zn.pr, atol, rtol);
+            s += sq_ratio(TT_E(pth), z.pth, zn.pth, atol, rtol);
+#undef TT_E
+#undef TT_HS
+#undef TT_C2
+#undef TT_C3
+#undef TT_C4
+#undef TT_C5
+#undef TT_C6
+#undef TT_C7
+            s *= (1.0 / 3.0);
+            if (!(s <= worst)) worst = s;
+            z = zn;
+            g = k7;
+        }
+        r_out = z.r;
+        if (worst <= 1.0) break;
+    }
+    return r_out;
+}
+
+// Paper's method (Sec. 3.2): bisection of theta(lambda) - pi/2 on the cubic-
+// Hermite interpolant of the accepted step, to 1e-12 in lambda.
+static __device__ double refine_hermite64(const State& y0, const State& f0, const State& y1,
+                                   const State& f1, double h) {
+    double lo = 0.0, hi = 1.0;
+    const bool s0 = y0.th <= kHalfPi;
+    for (int it = 0; it < 200 && (hi - lo) * h > 1e-12; ++it) {
+        double mid = 0.5 * (lo + hi);
+        double B[4], dB[4];
+        hermite4(mid, B, dB);
+        double th = B[0] * y0.th + B[1] * h * f0.th + B[2] * y1.th + B[3] * h * f1.th;
+        if ((th <= kHalfPi) == s0) lo = mid;
+        else hi = mid;
+    }
+    double sc = 0.5 * (lo + hi);
+    double B[4], dB[4];
+    hermite4(sc, B, dB);
+    return B[0] * y0.r + B[1] * h * f0.r + B[2] * y1.r + B[3] * h * f1.r;
+}
+
+// Hairer-Norsett-Wanner starting step (embedded order 4), four-component norm.
+template <int METRIC>
+__device__ double initial_step64(const ImageDesc& d, const KerrK& kk, const RayConst& R,
+                                 const State& y0, const State& f0, double atol, double rtol) {
+    double sr = fma(rtol, fabs(y0.r), atol), st = fma(rtol, fabs(y0.th), atol);
+    double sp = fma(rtol, fabs(y0.pr), atol), sq = fma(rtol, fabs(y0.pth), atol);
+    double d0 = sqrt(0.25 * ((y0.r / sr) * (y0.r / sr) + (y0.th / st) * (y0.th / st) +
+                             (y0.pr / sp) * (y0.pr / sp) + (y0.pth / sq) * (y0.pth / sq)));
+    double d1 = sqrt(0.25 * ((f0.r / sr) * (f0.r / sr) + (f0.th / st) * (f0.th / st) +
+                             (f0.pr / sp) * (f0.pr / sp) + (f0.pth / sq) * (f0.pth / sq)));
+    double h0 = (d0 < 1e-5 || d1 < 1e-5) ? 1e-6 : 0.01 * d0 / d1;
+    State y1, f1;
+    y1.r = y0.r + h0 * f0.r;
+    y1.th = y0.th + h0 * f0.th;
+    y1.pr = y0.pr + h0 * f0.pr;
+    y1.pth = y0.pth + h0 * f0.pth;
+    double H1;
+    flow64<METRIC>(d, kk, R, y1, f1, H1);
+    double q0 = (f1.r - f0.r) / sr, q1 = (f1.th - f0.th) / st;
+    double q2 = (f1.pr - f0.pr) / sp, q3 = (f1.pth - f0.pth) / sq;
+    double d2 = sqrt(0.25 * (q0 * q0 + q1 * q1 + q2 * q2 + q3 * q3)) / h0;
+    double dm = fmax(d1, d2);
+    double h1 = (dm <= 1e-15) ? fmax(1e-6, h0 * 1e-3) : pow(0.01 / dm, 0.2);
+    return fmin(100.0 * h0, h1);
+}
+
+// ---------------------------------------------------------------------------
+// Per-lane ray record.
+// ---------------------------------------------------------------------------
+struct Lane {
+    const ImageDesc* d;
+    long long q;            // output index within the image
+    State y, k1;            // FP64 state and its flow (first-same-as-last, valid if k64_ok)
+    RayConst R;
+    KerrK kk;
+    double h, lam, hmax, inten;
+    int steps, rejects, ncross, nrec, code;
+    bool last_rej;
+    // a disk crossing waiting for its (batched) refinement: the start of its step
+    bool pend;
+    State yc;
+    // mixed precision
+    StateF k1f;             // FP32 flow at the state (valid if k32_ok)
+    StateF lo;              // low parts of the compensated FP32-pair state
+    RayConstF Rf;
+    float Mf, a2f, rpmf;    // M, a^2, r_+ - r_-
+    float rph, rpl;         // r_+ as an FP32 pair
+    float caph, capl;       // capture radius as an FP32 pair
+    float escf, fp64f;      // escape radius, FP64-step radius
+    float thpf;             // FP64 steps within this angle of the axis
+    float hf, lamf;         // step size and affine parameter of the FP32 steps
+    bool k64_ok, k32_ok;
+};
+
+__device__ __forceinline__ void write_final(const Lane& L, int code) {
+    const ImageDesc& d = *L.d;
+    const long long q = L.q, n = d.pix_count;
+    d.code[q] = (int8_t)code;
+    d.n_cross[q] = (int8_t)min(L.ncross, 127);
+    d.intensity[q] = L.inten;
+    d.h_max[q] = L.hmax;
+    d.steps[q] = L.steps;
+    d.rejects[q] = L.rejects;
+    for (int k = L.nrec; k < kMaxCross; ++k) {
+        d.r_cross[k * n + q] = 0.0;
+        d.g[k * n + q] = 0.0;
+        d.I_cross[k * n + q] = 0.0;
+    }
+}
+
+__device__ __forceinline__ void split_pair(double x, float& hi, float& lo) {
+    hi = (float)x;
+    lo = (float)(x - (double)hi);
+}
+
+__device__ __forceinline__ State pair_to64(const StateF& hi, const StateF& lo) {
+    return State{(double)hi.r + (double)lo.r, (double)hi.th + (double)lo.th, (double)hi.pr + (double)lo.pr,
+                 (double)hi.pth + (double)lo.pth};
+}
+
+__device__ __forceinline__ void split_state(const State& y, StateF& hi, StateF& lo) {
+    split_pair(y.r, hi.r, lo.r);
+    split_pair(y.th, hi.th, lo.th);
+    split_pair(y.pr, hi.pr, lo.pr);
+    split_pair(y.pth, hi.pth, lo.pth);
+}
+
+// The Hairer-Norsett-Wanner starting step in FP32 for the mixed paths, from the
+// FP32 flow k1f at yf (already in L).
+static __device__ float initial_step32(const Lane& L, const StateF& y0, float dr0, float atol, float rtol) {
+    const StateF f0 = L.k1f;
+    const float sr = fmaf(rtol, fabsf(y0.r), atol), st = fmaf(rtol, fabsf(y0.th), atol);
+    const float sp = fmaf(rtol, fabsf(y0.pr), atol), sq = fmaf(rtol, fabsf(y0.pth), atol);
+    auto n4 = [&](float a, float b, float c, float e) {
+        return sqrtf(0.25f * (a / sr * (a / sr) + b / st * (b / st) + c / sp * (c / sp) + e / sq * (e / sq)));
+    };
+    const float d0 = n4(y0.r, y0.th, y0.pr, y0.pth);
+    const float d1 = n4(f0.r, f0.th, f0.pr, f0.pth);
+    const float h0 = (d0 < 1e-5f || d1 < 1e-5f) ? 1e-6f : 0.01f * d0 / d1;
+    const StateF y1 = {fmaf(h0, f0.r, y0.r), fmaf(h0, f0.th, y0.th), fmaf(h0, f0.pr, y0.pr), fmaf(h0, f0.pth, y0.pth)};
+    StateF f1;
+    float H1;
+    kerr_flow32(L.Mf, L.a2f, L.rpmf, L.Rf, y1, fmaf(h0, f0.r, dr0), f1, H1);
+    const float d2 = n4(f1.r - f0.r, f1.th - f0.th, f1.pr - f0.pr, f1.pth - f0.pth) / h0;
+    const float dm = fmaxf(d1, d2);
+    const float h1 = (dm <= 1e-15f) ? fmaxf(1e-6f, h0 * 1e-3f) : __powf(0.01f / dm, 0.2f);
+    return fminf(100.0f * h0, h1);
+}
+
+// Initial data from the ZAMO tetrad (paper Sec. 2.2), time-reversed. Returns
+// false (and writes a BADPIXEL record) if the pixel is outside the sky.
+template <int METRIC>
+__device__ bool init_ray(Lane& L, const ImageDesc* d_ptr, long long q, const SolverDesc& sol) {
+    const ImageDesc& d = *d_ptr;
+    L.d = d_ptr;
+    L.q = q;
+    L.kk = make_kerr(d.M, d.a);
+    L.steps = 0;
+    L.rejects = 0;
+    L.ncross = 0;
+    L.nrec = 0;
+    L.code = -1;
+    L.inten = 0.0;
+    L.hmax = 0.0;
+    L.lam = 0.0;
+    L.last_rej = false;
+    L.pend = false;
+    const long long p = d.pix_begin + q;
+    const long long i = p % d.nx, j = p / d.nx;
+    const double alpha = d.alpha_min + ((double)i + 0.5) * d.dalpha;
+    const double beta = d.beta_min + ((double)j + 0.5) * d.dbeta;
+    const double D = d.r_obs, th = d.theta_obs;
+    const double rho2 = alpha * alpha + beta * beta;
+    if (!isfinite(alpha) || !isfinite(beta) || !(rho2 < D * D)) {
+        write_final(L, 5);
+        return false;
+    }
+    // ZAMO tetrad at the observer: e_(t) = (1/N)(dt + omega dphi), e_(i) = d_i / sqrt(g_ii)
+    double g[5], omN, iN, ir, ith, iph;
+    if (d.obs_ready) {
+        for (int k = 0; k < 5; ++k) g[k] = d.obs_g[k];
+        omN = d.obs_omN;
+        iN = d.obs_iN;
+        ir = d.obs_ir;
+        ith = d.obs_ith;
+        iph = d.obs_iph;
+    } else {
+        lower64<METRIC>(d, D, th, g);
+        const double omega = -g[1] / g[4];
+        const double N = sqrt(-g[0] + omega * omega * g[4]);
+        iN = 1.0 / N;
+        omN = omega * iN;
+        ir = 1.0 / sqrt(g[2]);
+        ith = 1.0 / sqrt(g[3]);
+        iph = 1.0 / sqrt(g[4]);
+    }
+    const double gtt = g[0], gtp = g[1], grr = g[2], gthth = g[3], gpp = g[4];
+    const double pl_r = sqrt(1.0 - rho2 / (D * D));
+    const double pu_t = iN;
+    const double pu_r = pl_r * ir;
+    const double pu_th = (beta / D) * ith;
+    const double pu_ph = omN + (-alpha / D) * iph;
+    const double p_t = gtt * pu_t + gtp * pu_ph;
+    const double p_r = grr * pu_r;
+    const double p_th = gthth * pu_th;
+    const double p_ph = gtp * pu_t + gpp * pu_ph;
+    L.y.r = D;
+    L.y.th = th;
+    L.y.pr = -p_r;
+    L.y.pth = -p_th;
+    L.R = make_ray_const(d.a, -p_t, -p_ph);
+    L.k32_ok = false;
+    if (sol.precision == 0) {
+        double H0;
+        flow64<METRIC>(d, L.kk, L.R, L.y, L.k1, H0);
+        L.hmax = fabs(H0);
+        L.h = (sol.h0 > 0.0) ? sol.h0 : initial_step64<METRIC>(d, L.kk, L.R, L.y, L.k1, sol.atol, sol.rtol);
+        L.k64_ok = true;
+    } else {
+        // mixed paths: FP32 flow and starting step; |H(y0)| is ~1e-16 and not sampled
+        L.k64_ok = false;
+        L.Rf = to_float(L.R, d.M);
+        L.Mf = (float)d.M;
+        L.a2f = (float)(d.a * d.a);
+        L.rpmf = (float)(d.r_plus - d.r_minus);
+        split_pair(d.r_plus, L.rph, L.rpl);
+        split_pair(d.r_capture, L.caph, L.capl);
+        L.escf = (float)d.r_escape;
+        L.fp64f = (float)d.r_fp64;
+        L.thpf = (float)d.th_pole;
+        L.lamf = 0.0f;
+        const StateF yf = {(float)L.y.r, (float)L.y.th, (float)L.y.pr, (float)L.y.pth};
+        const float dr0 = (float)(L.y.r - d.r_plus);
+        float H0;
+        kerr_flow32(L.Mf, L.a2f, L.rpmf, L.Rf, yf, dr0, L.k1f, H0);
+        L.k32_ok = true;
+        L.hf = (sol.h0 > 0.0) ? (float)sol.h0 : initial_step32(L, yf, dr0, (float)sol.atol, (float)sol.rtol);
+        L.h = (double)L.hf;
+    }
+    return true;
+}
+
+// Emission at a refined crossing radius (paper Sec. 2.3-2.4): counted if on the
+// disk, stored (r, g, g^4 F) while slots remain.
+template <int METRIC>
+__device__ __forceinline__ void record_crossing(Lane& L, double rc) {
+    const ImageDesc& d = *L.d;
+    if (rc >= d.r_in && rc <= d.r_out) {
+        if (L.nrec < d.max_cross) {
+            const double gf = redshift64<METRIC>(d, rc, L.R.pt, L.R.pph);
+            const double F = flux64(d, rc);
+            const double g2 = gf * gf;
+            const double I = g2 * g2 * F;
+            const long long n = d.pix_count, q = L.q;
+            d.r_cross[L.nrec * n + q] = rc;
+            d.g[L.nrec * n + q] = gf;
+            d.I_cross[L.nrec * n + q] = I;
+            L.inten += I;
+            L.nrec++;
+        }
+        L.ncross++;
+    }
+}
+
+// Refine the pending crossing from the start of its step and record it.
+template <int METRIC>
+__device__ void refine_pending(Lane& L, const SolverDesc& sol) {
+    const ImageDesc& d = *L.d;
+    State f0;
+    double H0;
+    flow64<METRIC>(d, L.kk, L.R, L.yc, f0, H0);
+    L.hmax = fmax(L.hmax, fabs(H0));
+    const double rc = refine_henon64<METRIC>(d, L.kk, L.R, L.yc, f0, sol.atol, sol.rtol);
+    record_crossing<METRIC>(L, rc);
+    L.pend = false;
+}
+
+// A crossing was found in the step that starts at y (FP64).  Henon refinement
+// is deferred to a batched phase; crossings stay in order along the ray.
+template <int METRIC>
+__device__ __forceinline__ void note_crossing(Lane& L, const State& y, const SolverDesc& sol) {
+    if (L.pend) refine_pending<METRIC>(L, sol);
+    L.yc = y;
+    L.pend = true;
+}
+
+// One FP64 step attempt; returns the termination code or -1 if the ray continues.
+template <int METRIC>
+__device__ int step_ray64(Lane& L, const SolverDesc& sol) {
+    const ImageDesc& d = *L.d;
+    if ((long long)L.steps + (long long)L.rejects >= sol.max_steps) return 2;
+    const double hmin = (sol.h_min > 0.0) ? sol.h_min : 1e-14 * fmax(1.0, fabs(L.lam));
+    if (L.h < hmin) return 3;
+    State yn, kn, e;
+    double Hn;
+    dp5_step64<METRIC>(d, L.kk, L.R, L.y, L.k1, L.h, yn, kn, Hn, e);
+    const double err2 = err_norm2(L.y, yn, e, sol.atol, sol.rtol);
+    if (isnan(err2) || !isfinite(yn.r) || !isfinite(yn.th) || !isfinite(yn.pr) || !isfinite(yn.pth))
+        return 4;
+    if (err2 <= 1.0) {
+        L.steps++;
+        if (d.disk && ((L.y.th <= kHalfPi) != (yn.th <= kHalfPi))) {
+            if (sol.refine == 1) {
+                const double rc = refine_hermite64(L.y, L.k1, yn, kn, L.h);
+                if (L.pend) refine_pending<METRIC>(L, sol);
+                record_crossing<METRIC>(L, rc);
+            } else {
+                note_crossing<METRIC>(L, L.y, sol);
+            }
+        }
+        L.lam += L.h;
+        L.y = yn;
+        L.k1 = kn;
+        L.hmax = fmax(L.hmax, fabs(Hn));
+        if (yn.r < d.r_capture) return 1;
+        if (yn.r > d.r_escape) return 0;
+        const double fac = fmin(L.last_rej ? 1.0 : 10.0, fmax(0.2, step_factor(err2)));
+        L.h *= fac;
+        L.last_rej = false;
+    } else {
+        L.rejects++;
+        L.h *= fmax(0.2, step_factor(err2));
+        L.last_rej = true;
+    }
+    return -1;
+}
+
+// ---------------------------------------------------------------------------
+// Mixed precision (closed-form Kerr).  The seven stages, the flow, the error
+// estimate and norm and the step-size control run in FP32.  The state is
+// accumulated either in FP64 (ACC 0: y_new = y + (double)(h sum b_i k_i)) or as
+// a compensated FP32 pair (ACC 1: hi + lo with TwoSum, ~48 bits), which needs
+// no FP64 instruction in the step.  Steps that start below r_fp64 run in FP64;
+// crossings are refined in FP64.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float sq_ratio32(float e, float y, float yn, float atol, float rtol) {
+    float sc = fmaf(rtol, fmaxf(fabsf(y), fabsf(yn)), atol);
+    float q = __fdividef(e, sc);
+    return q * q;
+}
+
+// hi + lo <- hi + lo + x (Knuth's TwoSum, then renormalised).
+__device__ __forceinline__ void pair_add(float& hi, float& lo, float x) {
+    float s = hi + x;
+    float bb = s - hi;
+    float err = (hi - (s - bb)) + (x - bb);
+    float l = lo + err;
+    hi = s + l;
+    lo = l - (hi - s);
+}
+
+// sign of (hi + lo) - (ch + cl), exact enough whenever the difference exceeds ~1e-14 relative
+__device__ __forceinline__ bool pair_below(float hi, float lo, float ch, float cl) {
+    return ((hi - ch) + (lo - cl)) < 0.0f;
+}
+
+template <int ACC>
+__device__ int step_ray32(Lane& L, StateF& yhi, const SolverDesc& sol) {
+    const ImageDesc& d = *L.d;
+    if ((long long)L.steps + (long long)L.rejects >= sol.max_steps) return 2;
+    const float h = L.hf;
+    const float hmin = (sol.h_min > 0.0) ? (float)sol.h_min : 1e-14f * fmaxf(1.0f, L.lamf);
+    if (h < hmin) return 3;
+    using namespace dp;
+    StateF y;
+    float dr0;
+    if (ACC == 0) {
+        y = StateF{(float)L.y.r, (float)L.y.th, (float)L.y.pr, (float)L.y.pth};
+        dr0 = (float)(L.y.r - d.r_plus);
+    } else {
+        y = yhi;
+        dr0 = (y.r - L.rph) + (L.lo.r - L.rpl);
+    }
+    float Hs;
+    if (!L.k32_ok) {
+        kerr_flow32(L.Mf, L.a2f, L.rpmf, L.Rf, y, dr0, L.k1f, Hs);
+        L.k32_ok = true;
+    }
+    const StateF k1 = L.k1f;
+    StateF k2, k3, k4, k5, k6, k7, ys;
+#define TT_FS(dst, er, et, ep, eq)                         \
+    ys.r = fmaf(h, (er), y.r);                             \
+    ys.th = fmaf(h, (et), y.th);                           \
+    ys.pr = fmaf(h, (ep), y.pr);                           \
+    ys.pth = fmaf(h, (eq), y.pth);                         \
+    kerr_flow32(L.Mf, L.a2f, L.rpmf, L.Rf, ys, fmaf(h, (er), dr0), dst, Hs);
+#define TT_C2(f) ((float)a21 * k1.f)
+#define TT_C3(f) fmaf((float)a32, k2.f, (float)a31 * k1.f)
+#define TT_C4(f) fmaf((float)a43, k3.f, fmaf((float)a42, k2.f, (float)a41 * k1.f))
+#define TT_C5(f) fmaf((float)a54, k4.f, fmaf((float)a53, k3.f, fmaf((float)a52, k2.f, (float)a51 * k1.f)))
+#define TT_C6(f) \
+    fmaf((float)a65, k5.f, fmaf((float)a64, k4.f, fmaf((float)a63, k3.f, fmaf((float)a62, k2.f, (float)a61 * k1.f))))
+#define TT_C7(f) \
+    fmaf((float)b6, k6.f, fmaf((float)b5, k5.f, fmaf((float)b4, k4.f, fmaf((float)b3, k3.f, (float)b1 * k1.f))))
+    TT_FS(k2, TT_C2(r), TT_C2(th), TT_C2(pr), TT_C2(pth))
+    TT_FS(k3, TT_C3(r), TT_C3(th), TT_C3(pr), TT_C3(pth))
+    TT_FS(k4, TT_C4(r), TT_C4(th), TT_C4(pr), TT_C4(pth))
+    TT_FS(k5, TT_C5(r), TT_C5(th), TT_C5(pr), TT_C5(pth))
+    TT_FS(k6, TT_C6(r), TT_C6(th), TT_C6(pr), TT_C6(pth))
+    StateF inc;
+    inc.r = h * TT_C7(r);
+    inc.th = h * TT_C7(th);
+    inc.pr = h * TT_C7(pr);
+    inc.pth = h * TT_C7(pth);
+    StateF yn = {y.r + inc.r, y.th + inc.th, y.pr + inc.pr, y.pth + inc.pth};
+    float Hn;
+    kerr_flow32(L.Mf, L.a2f, L.rpmf, L.Rf, yn, dr0 + inc.r, k7, Hn);
+#define TT_E(f) \
+    h * fmaf((float)e7, k7.f, fmaf((float)e6, k6.f, fmaf((float)e5, k5.f, fmaf((float)e4, k4.f, \
+             fmaf((float)e3, k3.f, (float)e1 * k1.f)))))
+    const float atol = (float)sol.atol, rtol = (float)sol.rtol;
+    float err2 = sq_ratio32(TT_E(r), y.r, yn.r, atol, rtol);
+    err2 += sq_ratio32(TT_E(th), y.th, yn.th, atol, rtol);
+    err2 += sq_ratio32(TT_E(pr), y.pr, yn.pr, atol, rtol);
+    err2 += sq_ratio32(TT_E(pth), y.pth, yn.pth, atol, rtol);
+    err2 *= 0.25f;
+#undef TT_E
+#undef TT_FS
+#undef TT_C2
+#undef TT_C3
+#undef TT_C4
+#undef TT_C5
+#undef TT_C6
+#undef TT_C7
+    if (isnan(err2) || !isfinite(yn.r) || !isfinite(yn.th) || !isfinite(yn.pr) || !isfinite(yn.pth)) return 4;
+    if (err2 <= 1.0f) {
+        L.steps++;
+        bool captured, escaped;
+        if (ACC == 0) {
+            State y64n;
+            y64n.r = L.y.r + (double)inc.r;
+            y64n.th = L.y.th + (double)inc.th;
+            y64n.pr = L.y.pr + (double)inc.pr;
+            y64n.pth = L.y.pth + (double)inc.pth;
+            if (d.disk && ((L.y.th <= kHalfPi) != (y64n.th <= kHalfPi))) note_crossing<0>(L, L.y, sol);
+            L.y = y64n;
+            captured = y64n.r < d.r_capture;
+            escaped = y64n.r > d.r_escape;
+        } else {
+            StateF hi = yhi, lo = L.lo;
+            pair_add(hi.r, lo.r, inc.r);
+            pair_add(hi.th, lo.th, inc.th);
+            pair_add(hi.pr, lo.pr, inc.pr);
+            pair_add(hi.pth, lo.pth, inc.pth);
+            // pi/2 as an FP32 pair
+            const float pi2h = 1.57079637f, pi2l = -4.37113883e-08f;
+            const bool s0 = !pair_below(pi2h, pi2l, yhi.th, L.lo.th);     // theta <= pi/2 before
+            const bool s1 = !pair_below(pi2h, pi2l, hi.th, lo.th);        // and after
+            if (d.disk && s0 != s1) note_crossing<0>(L, pair_to64(yhi, L.lo), sol);
+            yhi = hi;
+            L.lo = lo;
+            captured = pair_below(hi.r, lo.r, L.caph, L.capl);
+            escaped = hi.r > L.escf;
+        }
+        L.lamf += h;
+        L.k1f = k7;
+        L.k64_ok = false;
+        if (captured) return 1;
+        if (escaped) return 0;
+        float fac = (err2 < 1e-30f) ? 10.0f : 0.9f * __powf(err2, -0.1f);
+        fac = fminf(L.last_rej ? 1.0f : 10.0f, fmaxf(0.2f, fac));
+        L.hf = h * fac;
+        L.last_rej = false;
+    } else {
+        L.rejects++;
+        L.hf = h * fmaxf(0.2f, 0.9f * __powf(err2, -0.1f));
+        L.last_rej = true;
+    }
+    return -1;
+}
+
+// FP64 |H| at the lane's current state (mixed-path monitor).
+template <int ACC>
+__device__ __forceinline__ void check_h64(Lane& L, const StateF& yhi) {
+    const State y = (ACC == 0) ? L.y : pair_to64(yhi, L.lo);
+    L.hmax = fmax(L.hmax, fabs(kerr_h64(L.kk, L.R, y)));
+}
+
+__device__ __forceinline__ int find_image(const ImageDesc* descs, int n, long long rid) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (descs[mid].ray_begin <= rid) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Lane states of the warp loop.
+enum : int { kIdle = 0, kRun = 1, kDone = 2 };
+
+// PREC 0: FP64.  PREC 1: mixed with FP64 accumulation.  PREC 2: mixed with the
+// compensated FP32-pair accumulation.
+template <int METRIC, int PREC>
+__device__ __forceinline__ void trace_loop(const ImageDesc* descs, int n_desc, long long total,
+                                           const SolverDesc& sol, const TuneParams& tp,
+                                           unsigned long long* queue) {
+    constexpr int ACC = (PREC == 2) ? 1 : 0;
+    const int lane = threadIdx.x & 31;
+    Lane L;
+    L.pend = false;
+    StateF yhi = {0.0f, 0.0f, 0.0f, 0.0f};   // pair accumulator: hi parts
+    int st = kIdle;
+    bool drained = false;
+    int wait64 = 0;
+    unsigned iter = 0;
+    for (;;) {
+        // ---- refill phase: flush finished rays, start new ones -------------
+        const int n_free = __popc(__ballot_sync(kFull, st != kRun));
+        if (n_free > 0 && (n_free >= tp.refill || n_free == 32) &&
+            (!drained || __any_sync(kFull, st == kDone))) {
+            if (st != kIdle && L.pend) refine_pending<METRIC>(L, sol);
+            if (st == kDone) {
+                if (PREC != 0) check_h64<ACC>(L, yhi);
+                write_final(L, L.code);
+                st = kIdle;
+            }
+            if (!drained) {
+                const unsigned idle = __ballot_sync(kFull, st == kIdle);
+                const int n_idle = __popc(idle);
+                unsigned long long base = 0;
+                if (lane == 0) base = atomicAdd(queue, (unsigned long long)n_idle);
+                base = __shfl_sync(kFull, base, 0);
+                if (base + (unsigned long long)n_idle >= (unsigned long long)total) drained = true;
+                if (st == kIdle) {
+                    const long long rid = (long long)base + __popc(idle & ((1u << lane) - 1u));
+                    if (rid < total) {
+                        const int im = (n_desc == 1) ? 0 : find_image(descs, n_desc, rid);
+                        if (init_ray<METRIC>(L, descs + im, rid - descs[im].ray_begin, sol)) {
+                            st = kRun;
+                            if (ACC == 1) split_state(L.y, yhi, L.lo);
+                        }
+                    }
+                }
+            }
+        }
+        const unsigned running = __ballot_sync(kFull, st == kRun);
+        if (!running) {
+            if (drained && !__any_sync(kFull, st == kDone)) break;
+            continue;
+        }
+        ++iter;
+        // ---- step phases ---------------------------------------------------
+        if (PREC == 0) {
+            if (st == kRun) {
+                const int code = step_ray64<METRIC>(L, sol);
+                if (code >= 0) {
+                    L.code = code;
+                    st = kDone;
+                }
+            }
+        } else {
+            bool want64 = false;
+            if (st == kRun) {
+                // FP64 near the horizon and near the axis (the coordinate singularities)
+                const float thf = (ACC == 0) ? (float)L.y.th : yhi.th;
+                const float rf = (ACC == 0) ? (float)L.y.r : yhi.r;
+                want64 = (rf < L.fp64f) || (thf < L.thpf) || (thf > 3.14159274f - L.thpf);
+            }
+            const unsigned w64 = __ballot_sync(kFull, want64);
+            if (w64) {
+                const bool run64 = (__popc(w64) >= tp.fp64_batch) || (w64 == running) || (wait64 >= tp.fp64_wait);
+                wait64 = run64 ? 0 : wait64 + 1;
+                if (run64 && want64) {
+                    if (ACC == 1) L.y = pair_to64(yhi, L.lo);
+                    if (!L.k64_ok) {
+                        double H;
+                        flow64<0>(*L.d, L.kk, L.R, L.y, L.k1, H);
+                        L.k64_ok = true;
+                    }
+                    L.k32_ok = false;
+                    L.h = (double)L.hf;
+                    const int code = step_ray64<0>(L, sol);
+                    L.hf = (float)L.h;
+                    if (ACC == 1) split_state(L.y, yhi, L.lo);
+                    if (code >= 0) {
+                        L.code = code;
+                        st = kDone;
+                    }
+                }
+            }
+            if (st == kRun && !want64) {
+                const int code = step_ray32<ACC>(L, yhi, sol);
+                if (code >= 0) {
+                    L.code = code;
+                    st = kDone;
+                }
+            }
+        }
+        // ---- batched crossing refinement -----------------------------------
+        const unsigned pend = __ballot_sync(kFull, st == kRun && L.pend);
+        if (pend && __popc(pend) >= tp.crossing_batch) {
+            if (st == kRun && L.pend) refine_pending<METRIC>(L, sol);
+        }
+        // ---- FP64 |H| monitor (mixed) --------------------------------------
+        if (PREC != 0 && (iter % (unsigned)tp.monitor_period) == 0) {
+            if (st == kRun) check_h64<ACC>(L, yhi);
+        }
+    }
+}
+
+int sm_count();
+
+// Persistent launch: as many blocks as fit (or blocks_per_sm) on every SM, no
+// more than the rays need.
+template <int N, typename K>
+cudaError_t launch_persistent(K kern, int block, int blocks_per_sm, const LaunchParams<N>& p, cudaStream_t st) {
+    int occ = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, block, 0);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) occ = 1;
+    int bps = blocks_per_sm > 0 ? min(blocks_per_sm, occ) : occ;
+    long long warps_needed = (p.total + 31) / 32;
+    long long grid = (long long)bps * sm_count();
+    long long grid_cap = (warps_needed * 32 + block - 1) / block;
+    if (grid > grid_cap) grid = grid_cap;
+    if (grid < 1) grid = 1;
+    kern<<<(unsigned)grid, block, 0, st>>>(p);
+    return cudaGetLastError();
+}
+
+// Fill the launch parameters (defaults for zero tune fields).
+template <int N>
+void fill_params(LaunchParams<N>& p, const ImageDesc* descs, int n, long long total, const SolverDesc& sol,
+                 const LaunchShape& shape, unsigned long long* queue) {
+    p.sol = sol;
+    p.n_desc = n;
+    // defaults: the FP64 path steps every lane in FP64 anyway, so it refills and
+    // refines in small batches; the mixed paths batch their FP64 work harder
+    const bool mixed = sol.precision != 0;
+    p.tune.refill = shape.refill > 0 ? shape.refill : (mixed ? 16 : 4);
+    p.tune.crossing_batch = shape.crossing_batch > 0 ? shape.crossing_batch : (mixed ? 16 : 8);
+    p.tune.fp64_batch = shape.fp64_batch > 0 ? shape.fp64_batch : 16;
+    p.tune.monitor_period = shape.monitor_period > 0 ? shape.monitor_period : 32;
+    p.tune.fp64_wait = shape.fp64_wait > 0 ? shape.fp64_wait : 64;
+    p.total = total;
+    p.queue = queue;
+    for (int i = 0; i < n; ++i) p.desc[i] = descs[i];
+}
+
+// Mixed-precision launches (tt_kernel_mixed.cu).
+cudaError_t launch_mixed(const ImageDesc* descs, int n, long long total, const SolverDesc& sol,
+                         const LaunchShape& shape, unsigned long long* queue, cudaStream_t stream);
+
+}  // namespace tt

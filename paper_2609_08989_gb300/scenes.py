@@ -26,7 +26,7 @@ from typing import List, Optional
 
 import numpy as np
 
-FP64, MIXED = 0, 1
+FP64, MIXED, MIXED_PAIR = 0, 1, 2
 REFINE_HENON, REFINE_HERMITE = 0, 1
 METRIC_KERR, METRIC_TABLE = 0, 1
 
@@ -60,6 +60,8 @@ class Scene:
     horizon_eps: float = 1e-3
     escape_factor: float = 1.1
     refine: int = REFINE_HENON
+    fp64_radius_factor: float = 0.0   # mixed paths: FP64 steps below factor * r_h (0: 1.5, < 0: none)
+    fp64_pole_sin: float = 0.0        # mixed paths: FP64 steps where sin(theta) < this (0: 0.1, < 0: none)
     # disk
     disk_enabled: int = 0
     r_in: float = 0.0            # <= 0: ISCO

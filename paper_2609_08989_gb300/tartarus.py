@@ -44,7 +44,7 @@ class TTSolver(C.Structure):
     _fields_ = [("method", C.c_int), ("precision", C.c_int), ("rtol", C.c_double), ("atol", C.c_double),
                 ("h0", C.c_double), ("h_min", C.c_double), ("max_steps", C.c_longlong),
                 ("horizon_eps", C.c_double), ("escape_factor", C.c_double), ("refine", C.c_int),
-                ("fp64_radius_factor", C.c_double)]
+                ("fp64_radius_factor", C.c_double), ("fp64_pole_sin", C.c_double)]
 
 
 class TTDisk(C.Structure):
@@ -59,7 +59,9 @@ class TTOutputs(C.Structure):
 
 
 class TTTune(C.Structure):
-    _fields_ = [("block", C.c_int), ("reg_variant", C.c_int), ("refill", C.c_int), ("blocks_per_sm", C.c_int)]
+    _fields_ = [("block", C.c_int), ("reg_variant", C.c_int), ("refill", C.c_int), ("blocks_per_sm", C.c_int),
+                ("crossing_batch", C.c_int), ("fp64_batch", C.c_int), ("monitor_period", C.c_int),
+                ("fp64_wait", C.c_int)]
 
 
 class TTImage(C.Structure):
@@ -191,7 +193,8 @@ def _camera(sc: Scene, pix_begin: int, pix_count: int) -> TTCamera:
 def solver_struct(sc: Scene) -> TTSolver:
     return TTSolver(method=0, precision=sc.precision, rtol=sc.rtol, atol=sc.atol, h0=sc.h0, h_min=sc.h_min,
                     max_steps=sc.max_steps, horizon_eps=sc.horizon_eps, escape_factor=sc.escape_factor,
-                    refine=sc.refine, fp64_radius_factor=getattr(sc, "fp64_radius_factor", 0.0))
+                    refine=sc.refine, fp64_radius_factor=sc.fp64_radius_factor,
+                    fp64_pole_sin=sc.fp64_pole_sin)
 
 
 def _disk(sc: Scene) -> TTDisk:
@@ -204,8 +207,7 @@ def _tune(tune) -> Optional[TTTune]:
         return None
     if isinstance(tune, TTTune):
         return tune
-    return TTTune(block=tune.get("block", 0), reg_variant=tune.get("reg_variant", 0),
-                  refill=tune.get("refill", 0), blocks_per_sm=tune.get("blocks_per_sm", 0))
+    return TTTune(**{f: int(tune.get(f, 0)) for f, _ in TTTune._fields_})
 
 
 def _npix(sc: Scene, pix_begin: int, pix_count: int) -> int:

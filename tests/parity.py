@@ -55,7 +55,7 @@ def in_band(orc, sc, pix, width=None):
 
 
 def compare(orc, sc, got, ref, pix, rel=1e-9, h_abs=1e-12, h_rel=5e-2, min_same_steps=0.98, report=None,
-            rel_diverged=None, h_ratio_only=False):
+            rel_diverged=None, h_ratio_only=False, h_ratio=2.0):
     """got/ref: dicts of numpy arrays for pixel indices pix (same order).
 
     h_ratio_only: compare every |H| maximum within a factor 2 (used for the
@@ -131,7 +131,7 @@ def compare(orc, sc, got, ref, pix, rel=1e-9, h_abs=1e-12, h_rel=5e-2, min_same_
     ratio = (np.maximum(g2, r2) + h_abs) / (np.minimum(g2, r2) + h_abs)
     worst["h_max_ratio_other"] = float(ratio.max()) if ratio.size else 1.0
     assert np.all(dh <= lim), "h_max (escaped) differs by %.3e" % dh.max()
-    assert np.all(ratio <= 2.0), "h_max (captured) differs by a factor %.2f" % ratio.max()
+    assert np.all(ratio <= h_ratio), "h_max (captured) differs by a factor %.2f" % ratio.max()
     same_steps = float(np.mean((got["steps"] == ref["steps"]) & (got["rejects"] == ref["rejects"])))
     worst["same_step_counts"] = same_steps
     assert same_steps >= min_same_steps, same_steps
