@@ -35,6 +35,9 @@ FP64_PEAK_TFLOPS = SM_COUNT * SM_MAX_MHZ * 1e6 * 2 * 2 / 1e12
 # counted from the kernel source (FMA = 2, add/mul/div/rcp/sqrt = 1, sin and cos 1 each):
 # 6 flow evaluations x 65 + stage combinations 232 + error norm 20 + step control 5.
 FLOPS_PER_STEP = 6 * 65 + 232 + 20 + 5
+# The same count for an FP32 step of the mixed paths (the rearranged FP32 flow is 72).
+FLOPS_PER_STEP_F32 = 6 * 72 + 232 + 20 + 5
+FP32_PEAK_TFLOPS = SM_COUNT * SM_MAX_MHZ * 1e6 * 128 * 2 / 1e12
 BYTES_OUT_PER_PIXEL = 3 * 3 * 8 + 8 + 8 + 4 + 4 + 1 + 1
 # host-to-device input of one step: the image descriptor (sizeof(tt::ImageDesc)) and the queue reset
 DESC_BYTES = 384 + 8
@@ -52,6 +55,9 @@ def parse():
     p.add_argument("--precision", default="fp64", choices=["fp64", "mixed", "mixed_pair"],
                    help="path of the main measurement (default: the FP64 headline)")
     p.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision objects")
+    p.add_argument("--workload", default="kerr_disk", choices=["kerr_disk", "batch", "table"],
+                   help="kerr_disk: the 1024^2 headline image (default); batch: 64 uneven images in one "
+                        "persistent launch, replayed from a CUDA graph; table: the 4096^2 tabulated-metric image")
     return p.parse_args()
 
 
@@ -327,10 +333,115 @@ def run_tartarus(args):
         dist.destroy_process_group()
 
 
+def run_workload(args):
+    """The batched (C4) and tabulated-metric (C5) workloads: same JSON line format."""
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from paper_2609_08989_gb300 import scenes, tartarus as T
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    T.lib()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    table = None
+    if args.workload == "batch":
+        imgs = scenes.batch_uneven(64, seed=2609, precision=scenes.MIXED_PAIR)
+        rays = sum(s.npix for s in imgs)
+        graph = T.TraceGraph(imgs)
+        step = graph.replay
+        launches_per_step = graph.launches_per_replay
+        outs = graph.outs
+        name = "batch_uneven_64_images_seed2609_mixed_pair"
+        dtype = "f32 stages / f32-pair state"
+        cfg = {"workload": name, "images": 64, "rays": rays, "res": [min(s.nx for s in imgs), max(s.nx for s in imgs)],
+               "rtol": imgs[0].rtol, "precision": "mixed_pair", "launch": "CUDA graph replay of one batch call"}
+        direct = lambda: T.trace_batch(imgs, outs)
+    else:
+        sc = scenes.table_kerr_with_nodes(args.n if args.n != 1024 else 4096)
+        table = T.Table(sc.table, sc.r_min, sc.r_max)
+        out = T.alloc_outputs(sc.npix)
+        rays = sc.npix
+        step = lambda: T.trace(sc, out=out, table=table, stream=stream)
+        launches_per_step = 1
+        outs = [out]
+        name = sc.name
+        dtype = "f64"
+        cfg = {"workload": name, "nx": sc.nx, "ny": sc.ny, "a": sc.a, "table": [512, 256], "rtol": sc.rtol,
+               "precision": "fp64"}
+        direct = None
+    for k in range(max(args.warmup, 0)):
+        flush.fill_(k & 0xFF)
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)
+        ev[k][0].record(stream)
+        step()
+        ev[k][1].record(stream)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    total_ms = t0.elapsed_time(t1)
+    tt = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    total_ms = float(tt.item())
+    kern_ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+    attempts = int(sum(o["steps"].sum().item() + o["rejects"].sum().item() for o in outs))
+    if rank == 0:
+        if args.workload == "batch":
+            flops = FLOPS_PER_STEP_F32 * attempts
+            peak, unit = FP32_PEAK_TFLOPS, "TFLOP/s"
+        else:
+            flops, peak, unit = None, FP64_PEAK_TFLOPS, "TFLOP/s"
+        line = {"metric": METRIC, "value": world * rays * args.steps / (total_ms / 1e3), "unit": UNIT,
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype,
+                "data": "synthetic", "config": cfg, "rk_step_attempts_per_step": attempts,
+                "gpu_launches": launches_per_step * args.steps, "clocks": clk,
+                "e2e": None}
+        if flops is not None:
+            ach = flops / (kern_ms / 1e3) / 1e12
+            line["roofline"] = {"bound": "alu", "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak,
+                                "traffic": None, "flops_per_unit": FLOPS_PER_STEP_F32,
+                                "unit_of_work": "FP32 Dormand-Prince step attempt (FP64 side work not counted)",
+                                "peak_source": "FP32 pipe: 152 SMs x 2070 MHz x 128 FFMA/clk (derived)"}
+        if direct is not None:
+            direct()
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            direct()
+            b.record(stream)
+            torch.cuda.synchronize()
+            line["direct_call"] = {"value": rays / (a.elapsed_time(b) / 1e3), "unit": UNIT,
+                                   "ms": a.elapsed_time(b)}
+        print(json.dumps(line), flush=True)
+    if table is not None:
+        table.destroy()
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload != "kerr_disk":
+        run_workload(args)
     else:
         run_tartarus(args)
 

@@ -153,7 +153,9 @@ typedef struct {
 
 /* Launch shape of the persistent kernel; NULL or zero fields select defaults.
  *   block           threads per block: 128 (default) or 256
- *   reg_variant     register-cap variant; only 0 (the compiler's choice) is built
+ *   reg_variant     registers per thread of the FP64 closed-form Kerr kernel at
+ *                   128 threads, single camera: 0 the compiler's choice, 1 at
+ *                   most 168, 2 at most 128 (other kernels ignore it)
  *   refill          flush finished rays and refill lanes once at least this many
  *                   lanes of a warp are done or idle (1..32, default 8)
  *   blocks_per_sm   persistent blocks per SM (0: as many as fit)

@@ -226,7 +226,7 @@ int check_shape(const tt_tune* t) {
     if (t->block != 0 && t->block != 128 && t->block != 256) return TT_EUNSUPPORTED;
     // built variants: 128 or 256 threads (FP64, closed-form Kerr), 128 (FP64 tables),
     // 256 (mixed paths)
-    if (t->reg_variant != 0) return TT_EUNSUPPORTED;
+    if (t->reg_variant < 0 || t->reg_variant > 2) return TT_EUNSUPPORTED;
     if (t->refill < 0 || t->refill > 32) return TT_EINVAL;
     if (t->blocks_per_sm < 0) return TT_EINVAL;
     if (t->crossing_batch < 0 || t->crossing_batch > 32) return TT_EINVAL;

@@ -13,6 +13,14 @@ __global__ void __launch_bounds__(256) trace_kernel64_b256(const __grid_constant
     trace_loop<METRIC, 0>(p.desc, p.n_desc, p.total, p.sol, p.tune, p.queue);
 }
 
+// Register-capped builds of the closed-form Kerr kernel (128 threads): at least
+// MINB resident blocks per SM caps registers at 65536 / (128 MINB) per thread
+// (MINB 3: 168, MINB 4: 128).
+template <int MINB>
+__global__ void __launch_bounds__(128, MINB) trace_kernel64_regcap(const __grid_constant__ LaunchParams<1> p) {
+    trace_loop<0, 0>(p.desc, p.n_desc, p.total, p.sol, p.tune, p.queue);
+}
+
 int sm_count() {
     static int n = 0;
     if (n == 0) {
@@ -34,6 +42,10 @@ static cudaError_t launch64(const ImageDesc* descs, int n, long long total, int 
     const int bps = shape.blocks_per_sm;
     if (metric_mode == 0) {
         if (shape.block == 256) return launch_persistent<N>(trace_kernel64_b256<0, N>, 256, bps, p, stream);
+        if constexpr (N == 1) {
+            if (shape.reg_variant == 1) return launch_persistent<N>(trace_kernel64_regcap<3>, 128, bps, p, stream);
+            if (shape.reg_variant == 2) return launch_persistent<N>(trace_kernel64_regcap<4>, 128, bps, p, stream);
+        }
         return launch_persistent<N>(trace_kernel64<0, N>, 128, bps, p, stream);
     }
     if (metric_mode == 1) return launch_persistent<N>(trace_kernel64<1, N>, 128, bps, p, stream);

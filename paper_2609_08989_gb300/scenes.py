@@ -122,6 +122,53 @@ def table_kerr(n: int = 4096, table: Optional[np.ndarray] = None, nr: int = 512,
                  rtol=1e-12, atol=1e-12, disk_enabled=1, r_out=30.0)
 
 
+def kerr_table_nodes(M: float, a: float, nr: int, nth: int, r_min: float, r_max: float) -> np.ndarray:
+    """Synthetic numerical metric: the Kerr spacetime sampled onto the table
+    format of include/tartarus.h ([nth, nr, 20]: for g_tt, g_tphi, g_thth,
+    g_phiphi and g^rr the value, d/dr, d/dth, d2/(dr dth)) -- input data for
+    the tabulated-metric path, standing in for a numerically generated metric."""
+    u = np.log(r_min) + np.arange(nr) * ((np.log(r_max) - np.log(r_min)) / (nr - 1))
+    r = np.exp(u)
+    r[0], r[-1] = r_min, r_max
+    th = np.pi * np.arange(nth) / (nth - 1)
+    s, c = np.sin(th), np.cos(th)
+    s[0] = s[-1] = 0.0
+    c[0], c[-1] = 1.0, -1.0
+    R, S, Cc = r[None, :], s[:, None], c[:, None]
+    a2 = a * a
+    r2 = R * R
+    Sig = r2 + a2 * Cc * Cc
+    Del = r2 - 2 * M * R + a2
+    q = R / Sig
+    q_r = (a2 * Cc * Cc - r2) / Sig ** 2
+    q_t = 2 * R * a2 * S * Cc / Sig ** 2
+    q_rt = 2 * a2 * S * Cc * (a2 * Cc * Cc - 3 * r2) / Sig ** 3
+    s2, sc, s4 = S * S, S * Cc, S ** 4
+    s3c = s2 * sc
+    out = np.zeros((nth, nr, 20))
+    f = [
+        (-1 + 2 * M * q, 2 * M * q_r, 2 * M * q_t, 2 * M * q_rt),
+        (-2 * M * a * s2 * q, -2 * M * a * s2 * q_r, -2 * M * a * (2 * sc * q + s2 * q_t),
+         -2 * M * a * (2 * sc * q_r + s2 * q_rt)),
+        (Sig, 2 * R + 0 * S, -2 * a2 * sc + 0 * R, 0 * R * S),
+        ((r2 + a2) * s2 + 2 * M * a2 * s4 * q, 2 * R * s2 + 2 * M * a2 * s4 * q_r,
+         (r2 + a2) * 2 * sc + 2 * M * a2 * (4 * s3c * q + s4 * q_t),
+         4 * R * sc + 2 * M * a2 * (4 * s3c * q_r + s4 * q_rt)),
+        (Del / Sig, ((2 * R - 2 * M) * Sig - Del * 2 * R) / Sig ** 2, 2 * a2 * sc * Del / Sig ** 2,
+         2 * a2 * sc * ((2 * R - 2 * M) * Sig - 4 * R * Del) / Sig ** 3),
+    ]
+    for k, comps in enumerate(f):
+        for j, v in enumerate(comps):
+            out[:, :, 4 * k + j] = np.broadcast_to(v, (nth, nr))
+    return out
+
+
+def table_kerr_with_nodes(n: int = 4096) -> Scene:
+    """The tabulated-metric workload with its synthetic Kerr table attached."""
+    sc = table_kerr(n)
+    return sc.replace(table=kerr_table_nodes(1.0, sc.a, 512, 256, sc.r_min, sc.r_max))
+
+
 # --------------------------------------------------------------------------
 # SplitMix64 (Steele, Lea & Flood, OOPSLA 2014), for the drawn batch of images.
 # --------------------------------------------------------------------------
@@ -158,7 +205,7 @@ def batch_uneven(n_images: int = 64, seed: int = 2609, precision: int = MIXED,
         sc = kerr_disk(n, precision).replace(
             name="batch_%02d" % k, a=a, theta_obs=deg(inc), alpha_min=-half, alpha_max=half,
             beta_min=-half, beta_max=half)
-        if precision == MIXED:
+        if precision != FP64:
             sc = sc.replace(rtol=MIXED_RTOL, atol=MIXED_RTOL)
         out.append(sc)
     return out

@@ -202,12 +202,22 @@ def _disk(sc: Scene) -> TTDisk:
                   max_crossings=sc.max_crossings, doppler=sc.doppler)
 
 
-def _tune(tune) -> Optional[TTTune]:
+def _tune(tune, sc: Optional[Scene] = None) -> Optional[TTTune]:
+    """Explicit shape, else the autotuned shape cached for this device and
+    workload class, else the library's built-in defaults (None)."""
+    if tune is None and sc is not None:
+        from . import autotune
+        tune = autotune.cached(sc)
     if tune is None:
         return None
     if isinstance(tune, TTTune):
         return tune
     return TTTune(**{f: int(tune.get(f, 0)) for f, _ in TTTune._fields_})
+
+
+def _tune_ref(tune, sc):
+    t = _tune(tune, sc)
+    return C.byref(t) if t is not None else None
 
 
 def _npix(sc: Scene, pix_begin: int, pix_count: int) -> int:
@@ -277,8 +287,7 @@ def trace(sc: Scene, out=None, stream=None, tune=None, table: Optional[Table] = 
         own = table = Table(sc.table, sc.r_min, sc.r_max)
     st = lib().tartarus_trace(C.byref(_metric(sc, table)), C.byref(TTObserver(sc.r_obs, sc.theta_obs)),
                               C.byref(_camera(sc, pix_begin, pix_count)), C.byref(solver_struct(sc)),
-                              C.byref(_disk(sc)), C.byref(_out_struct(out)),
-                              C.byref(_tune(tune)) if tune is not None else None, _stream_ptr(stream))
+                              C.byref(_disk(sc)), C.byref(_out_struct(out)), _tune_ref(tune, sc), _stream_ptr(stream))
     if own is not None:
         import torch
         torch.cuda.synchronize()
@@ -298,8 +307,8 @@ def trace_host(sc: Scene, out=None, stream=None, tune=None, table: Optional[Tabl
         own = table = Table(sc.table, sc.r_min, sc.r_max)
     st = lib().tartarus_trace_host(C.byref(_metric(sc, table)), C.byref(TTObserver(sc.r_obs, sc.theta_obs)),
                                    C.byref(_camera(sc, pix_begin, pix_count)), C.byref(solver_struct(sc)),
-                                   C.byref(_disk(sc)), C.byref(_out_struct(out)),
-                                   C.byref(_tune(tune)) if tune is not None else None, _stream_ptr(stream))
+                                   C.byref(_disk(sc)), C.byref(_out_struct(out)), _tune_ref(tune, sc),
+                                   _stream_ptr(stream))
     if own is not None:
         own.destroy()
     _check(st, "tartarus_trace_host")
@@ -323,8 +332,7 @@ def trace_batch(scenes: Sequence[Scene], outs=None, stream=None, tune=None,
         imgs[i].out = _out_struct(outs[i])
     status = (C.c_int * max(n, 1))()
     st = lib().tartarus_trace_batch(imgs, n, C.byref(solver_struct(scenes[0])),
-                                    C.byref(_tune(tune)) if tune is not None else None, status,
-                                    _stream_ptr(stream))
+                                    _tune_ref(tune, scenes[0] if n else None), status, _stream_ptr(stream))
     if status_out is not None:
         status_out[:] = list(status)[:n]
     if st != TT_OK and status_out is None:
@@ -350,13 +358,43 @@ def trace_batch_noalloc(scenes: Sequence[Scene], outs, stream=None, tune=None,
         imgs[i].out = _out_struct(outs[i])
     status = (C.c_int * max(n, 1))()
     st = lib().tartarus_trace_batch_noalloc(imgs, n, C.byref(solver_struct(scenes[0])),
-                                            C.byref(_tune(tune)) if tune is not None else None, status,
+                                            _tune_ref(tune, scenes[0] if n else None), status,
                                             _stream_ptr(stream))
     if status_out is not None:
         status_out[:] = list(status)[:n]
     if st != TT_OK and status_out is None:
         _check(st, "tartarus_trace_batch_noalloc")
     return outs
+
+
+class TraceGraph:
+    """A batch render captured once into a CUDA graph and replayed.
+
+    For repeated renders of the same images into the same output buffers (an
+    animation loop, a parameter scan that rewrites one set of outputs): the
+    descriptors are built and validated once, and each replay is one graph
+    launch.  The first (uncaptured) call also performs the library's one-time
+    per-device set-up, so capture itself makes no allocation."""
+
+    def __init__(self, scenes: Sequence[Scene], outs=None, tune=None,
+                 tables: Optional[Sequence[Optional[Table]]] = None):
+        import torch
+        self.scenes = list(scenes)
+        self.outs = outs if outs is not None else [alloc_outputs(s.npix) for s in self.scenes]
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            trace_batch(self.scenes, self.outs, stream=side, tune=tune, tables=tables)
+        torch.cuda.current_stream().wait_stream(side)
+        torch.cuda.synchronize()
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            trace_batch(self.scenes, self.outs, stream=torch.cuda.current_stream(), tune=tune, tables=tables)
+        self.launches_per_replay = (len(self.scenes) + 63) // 64
+
+    def replay(self):
+        self.graph.replay()
+        return self.outs
 
 
 def to_numpy(out) -> Dict[str, np.ndarray]:

@@ -169,3 +169,30 @@ def test_table_metric(T, orc):
     rel = np.abs(got["r_cross"][m] - ana["r_cross"][m]) / ana["r_cross"][m]
     print("table vs analytic: median %.2e  p99 %.2e" % (np.median(rel), np.percentile(rel, 99)))
     assert np.median(rel) < 1e-5
+
+
+def test_graph_replay_matches_direct(T):
+    imgs = scenes.batch_uneven(4, seed=7, precision=scenes.FP64, res_lo=16, res_hi=40)
+    direct = [T.to_numpy(o) for o in T.trace_batch(imgs)]
+    torch.cuda.synchronize()
+    g = T.TraceGraph(imgs)
+    for _ in range(2):
+        for o in g.outs:
+            for v in o.values():
+                v.fill_(-3)
+        outs = g.replay()
+        torch.cuda.synchronize()
+        for a, b in zip(outs, direct):
+            got = T.to_numpy(a)
+            for k in got:
+                assert np.array_equal(got[k], b[k]), k
+
+
+def test_register_capped_and_wide_variants_match(T):
+    sc = scenes.kerr_disk(64)
+    ref = run(T, sc)
+    for tune in (dict(reg_variant=1), dict(reg_variant=2), dict(block=256), dict(refill=1, crossing_batch=1),
+                 dict(refill=32, crossing_batch=32, blocks_per_sm=1)):
+        got = run(T, sc, tune=tune)
+        for k in ref:
+            assert np.array_equal(got[k], ref[k]), (tune, k)

@@ -108,3 +108,14 @@ def test_table_flow_matches_closed_form(orc):
         y[1], y[2] = rng.uniform(2.0, 30.0), rng.uniform(0.5, 2.6)
         d_t, d_k = orc.rhs(sc_t, y), orc.rhs(sc_k, y)
         assert np.max(np.abs(d_t - d_k)) < 1e-6 * max(1.0, np.max(np.abs(d_k)))
+
+
+def test_input_module_table_matches_oracle_sampler(orc):
+    """The input generator's Kerr table (used by the benchmark) equals the
+    oracle's sampler, whose fields are pinned symbolically in test_oracle_metric."""
+    a = 0.998
+    rh = 1.0 + math.sqrt(1 - a * a)
+    t1 = orc.kerr_table(1.0, a, 64, 33, rh, 1000.0)
+    t2 = scenes.kerr_table_nodes(1.0, a, 64, 33, rh, 1000.0)
+    scale = np.maximum(1.0, np.abs(t1))
+    assert np.max(np.abs(t1 - t2) / scale) < 1e-13
