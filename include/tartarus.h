@@ -67,6 +67,7 @@ extern "C" {
 #define TT_MIXED_PAIR    2   /* FP32 stages, compensated FP32-pair state accumulation (~48 bits) */
 #define TT_REFINE_HENON   0  /* exact step onto theta = pi/2 (default) */
 #define TT_REFINE_HERMITE 1  /* paper's cubic-Hermite bisection        */
+#define TT_REFINE_HENON64 2  /* Henon with FP64 stages on the mixed paths too (default there: FP32 stages) */
 
 typedef struct tt_table tt_table;        /* opaque device copy of a metric table */
 
@@ -111,7 +112,7 @@ typedef struct {
     double rtol, atol, h0, h_min;
     long long max_steps;
     double horizon_eps, escape_factor;
-    int refine;                 /* TT_REFINE_HENON or TT_REFINE_HERMITE */
+    int refine;                 /* TT_REFINE_HENON, TT_REFINE_HERMITE or TT_REFINE_HENON64 */
     double fp64_radius_factor;
     double fp64_pole_sin;
 } tt_solver;

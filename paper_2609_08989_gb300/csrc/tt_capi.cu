@@ -63,7 +63,8 @@ int check_solver(const tt_solver* s) {
     if (s->max_steps < 1) return TT_EINVAL;
     if (!is_finite(s->horizon_eps) || s->horizon_eps < 0.0) return TT_EINVAL;
     if (!is_finite(s->escape_factor) || !(s->escape_factor > 1.0)) return TT_EINVAL;
-    if (s->refine != TT_REFINE_HENON && s->refine != TT_REFINE_HERMITE) return TT_EINVAL;
+    if (s->refine != TT_REFINE_HENON && s->refine != TT_REFINE_HERMITE && s->refine != TT_REFINE_HENON64)
+        return TT_EINVAL;
     if (!is_finite(s->fp64_radius_factor) || !is_finite(s->fp64_pole_sin)) return TT_EINVAL;
     return TT_OK;
 }

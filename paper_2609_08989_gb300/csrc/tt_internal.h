@@ -62,7 +62,7 @@ struct ImageDesc {
 struct SolverDesc {
     double rtol, atol, h0, h_min;
     long long max_steps;
-    int refine;                   // 0 Henon, 1 Hermite
+    int refine;                   // 0 Henon, 1 Hermite, 2 Henon in FP64 on the mixed paths too
     int precision;                // 0 FP64, 1 mixed (FP64 state), 2 mixed (FP32-pair state)
 };
 

@@ -441,30 +441,124 @@ __device__ __forceinline__ void record_crossing(Lane& L, double rc) {
     }
 }
 
+__device__ __forceinline__ float sq_ratio32(float e, float y, float yn, float atol, float rtol) {
+    float sc = fmaf(rtol, fmaxf(fabsf(y), fabsf(yn)), atol);
+    float q = __fdividef(e, sc);
+    return q * q;
+}
+
+// Henon's exact step with FP32 stages (mixed paths): the same sub-stepping and
+// error rule as refine_henon64, the theta-system evaluated with the FP32 flow
+// at stage points formed from the FP64 sub-step start, and the sub-step
+// results accumulated in FP64.
+__device__ __forceinline__ void theta_flow32(const Lane& L, const StateF& y, float dr, StateF& g) {
+    StateF f;
+    float H;
+    kerr_flow32(L.Mf, L.a2f, L.rpmf, L.Rf, y, dr, f, H);
+    const float it = __frcp_rn(f.th);
+    g.r = f.r * it;
+    g.th = 1.0f;
+    g.pr = f.pr * it;
+    g.pth = f.pth * it;
+}
+
+static __device__ double refine_henon32(const Lane& L, const State& y0, double r_plus, float atol, float rtol) {
+    using namespace dp;
+    const double dth_all = kHalfPi - y0.th;
+    double r_out = y0.r;
+    StateF g0;
+    theta_flow32(L, StateF{(float)y0.r, (float)y0.th, (float)y0.pr, (float)y0.pth}, (float)(y0.r - r_plus), g0);
+    for (int m = 0; m <= 6; ++m) {
+        const int nsub = 1 << m;
+        const double dl64 = dth_all / (double)nsub;
+        const float dl = (float)dl64;
+        State z = y0;
+        StateF g = g0;
+        float worst = 0.0f;
+        for (int q = 0; q < nsub; ++q) {
+            const StateF zf = {(float)z.r, (float)z.th, (float)z.pr, (float)z.pth};
+            const float dr0 = (float)(z.r - r_plus);
+            StateF k2, k3, k4, k5, k6, k7, zs;
+#define TT_HS(dst, cc, er, ep, eq)                        \
+    zs.r = fmaf(dl, (er), zf.r);                          \
+    zs.pr = fmaf(dl, (ep), zf.pr);                        \
+    zs.pth = fmaf(dl, (eq), zf.pth);                      \
+    zs.th = fmaf(dl, (float)(cc), zf.th);                 \
+    theta_flow32(L, zs, fmaf(dl, (er), dr0), dst);
+#define TT_C2(f) ((float)a21 * g.f)
+#define TT_C3(f) fmaf((float)a32, k2.f, (float)a31 * g.f)
+#define TT_C4(f) fmaf((float)a43, k3.f, fmaf((float)a42, k2.f, (float)a41 * g.f))
+#define TT_C5(f) fmaf((float)a54, k4.f, fmaf((float)a53, k3.f, fmaf((float)a52, k2.f, (float)a51 * g.f)))
+#define TT_C6(f) \
+    fmaf((float)a65, k5.f, fmaf((float)a64, k4.f, fmaf((float)a63, k3.f, fmaf((float)a62, k2.f, (float)a61 * g.f))))
+#define TT_C7(f) \
+    fmaf((float)b6, k6.f, fmaf((float)b5, k5.f, fmaf((float)b4, k4.f, fmaf((float)b3, k3.f, (float)b1 * g.f))))
+            TT_HS(k2, c2, TT_C2(r), TT_C2(pr), TT_C2(pth))
+            TT_HS(k3, c3, TT_C3(r), TT_C3(pr), TT_C3(pth))
+            TT_HS(k4, c4, TT_C4(r), TT_C4(pr), TT_C4(pth))
+            TT_HS(k5, c5, TT_C5(r), TT_C5(pr), TT_C5(pth))
+            TT_HS(k6, 1.0, TT_C6(r), TT_C6(pr), TT_C6(pth))
+            const StateF inc = {dl * TT_C7(r), dl, dl * TT_C7(pr), dl * TT_C7(pth)};
+            const StateF zn = {zf.r + inc.r, zf.th + dl, zf.pr + inc.pr, zf.pth + inc.pth};
+            theta_flow32(L, zn, dr0 + inc.r, k7);
+#define TT_E(f) dl * fmaf((float)e7, k7.f, fmaf((float)e6, k6.f, fmaf((float)e5, k5.f, \
+                fmaf((float)e4, k4.f, fmaf((float)e3, k3.f, (float)e1 * g.f)))))
+            float s = sq_ratio32(TT_E(r), zf.r, zn.r, atol, rtol);
+            s += sq_ratio32(TT_E(pr), zf.pr, zn.pr, atol, rtol);
+            s += sq_ratio32(TT_E(pth), zf.pth, zn.pth, atol, rtol);
+#undef TT_E
+#undef TT_HS
+#undef TT_C2
+#undef TT_C3
+#undef TT_C4
+#undef TT_C5
+#undef TT_C6
+#undef TT_C7
+            s *= (1.0f / 3.0f);
+            if (!(s <= worst)) worst = s;
+            z.r += (double)inc.r;
+            z.th = y0.th + (double)(q + 1) * dl64;
+            z.pr += (double)inc.pr;
+            z.pth += (double)inc.pth;
+            g = k7;
+        }
+        r_out = z.r;
+        if (worst <= 1.0f) break;
+    }
+    return r_out;
+}
+
 // Refine the pending crossing from the start of its step and record it.
-template <int METRIC>
+// PREC 0: FP64 Henon.  Mixed paths: Henon with FP32 stages, or in FP64 when
+// the solver asks for it (refine 2); emission is evaluated in FP64 either way.
+template <int METRIC, int PREC>
 __device__ void refine_pending(Lane& L, const SolverDesc& sol) {
     const ImageDesc& d = *L.d;
-    State f0;
-    double H0;
-    flow64<METRIC>(d, L.kk, L.R, L.yc, f0, H0);
-    L.hmax = fmax(L.hmax, fabs(H0));
-    const double rc = refine_henon64<METRIC>(d, L.kk, L.R, L.yc, f0, sol.atol, sol.rtol);
+    double rc;
+    if (PREC != 0 && sol.refine != 2) {
+        rc = refine_henon32(L, L.yc, d.r_plus, (float)sol.atol, (float)sol.rtol);
+    } else {
+        State f0;
+        double H0;
+        flow64<METRIC>(d, L.kk, L.R, L.yc, f0, H0);
+        L.hmax = fmax(L.hmax, fabs(H0));
+        rc = refine_henon64<METRIC>(d, L.kk, L.R, L.yc, f0, sol.atol, sol.rtol);
+    }
     record_crossing<METRIC>(L, rc);
     L.pend = false;
 }
 
 // A crossing was found in the step that starts at y (FP64).  Henon refinement
 // is deferred to a batched phase; crossings stay in order along the ray.
-template <int METRIC>
+template <int METRIC, int PREC>
 __device__ __forceinline__ void note_crossing(Lane& L, const State& y, const SolverDesc& sol) {
-    if (L.pend) refine_pending<METRIC>(L, sol);
+    if (L.pend) refine_pending<METRIC, PREC>(L, sol);
     L.yc = y;
     L.pend = true;
 }
 
 // One FP64 step attempt; returns the termination code or -1 if the ray continues.
-template <int METRIC>
+template <int METRIC, int PREC>
 __device__ int step_ray64(Lane& L, const SolverDesc& sol) {
     const ImageDesc& d = *L.d;
     if ((long long)L.steps + (long long)L.rejects >= sol.max_steps) return 2;
@@ -481,10 +575,10 @@ __device__ int step_ray64(Lane& L, const SolverDesc& sol) {
         if (d.disk && ((L.y.th <= kHalfPi) != (yn.th <= kHalfPi))) {
             if (sol.refine == 1) {
                 const double rc = refine_hermite64(L.y, L.k1, yn, kn, L.h);
-                if (L.pend) refine_pending<METRIC>(L, sol);
+                if (L.pend) refine_pending<METRIC, PREC>(L, sol);
                 record_crossing<METRIC>(L, rc);
             } else {
-                note_crossing<METRIC>(L, L.y, sol);
+                note_crossing<METRIC, PREC>(L, L.y, sol);
             }
         }
         L.lam += L.h;
@@ -512,11 +606,6 @@ __device__ int step_ray64(Lane& L, const SolverDesc& sol) {
 // no FP64 instruction in the step.  Steps that start below r_fp64 run in FP64;
 // crossings are refined in FP64.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float sq_ratio32(float e, float y, float yn, float atol, float rtol) {
-    float sc = fmaf(rtol, fmaxf(fabsf(y), fabsf(yn)), atol);
-    float q = __fdividef(e, sc);
-    return q * q;
-}
 
 // hi + lo <- hi + lo + x (Knuth's TwoSum, then renormalised).
 __device__ __forceinline__ void pair_add(float& hi, float& lo, float x) {
@@ -535,6 +624,7 @@ __device__ __forceinline__ bool pair_below(float hi, float lo, float ch, float c
 
 template <int ACC>
 __device__ int step_ray32(Lane& L, StateF& yhi, const SolverDesc& sol) {
+    constexpr int PREC = ACC + 1;
     const ImageDesc& d = *L.d;
     if ((long long)L.steps + (long long)L.rejects >= sol.max_steps) return 2;
     const float h = L.hf;
@@ -611,7 +701,7 @@ __device__ int step_ray32(Lane& L, StateF& yhi, const SolverDesc& sol) {
             y64n.th = L.y.th + (double)inc.th;
             y64n.pr = L.y.pr + (double)inc.pr;
             y64n.pth = L.y.pth + (double)inc.pth;
-            if (d.disk && ((L.y.th <= kHalfPi) != (y64n.th <= kHalfPi))) note_crossing<0>(L, L.y, sol);
+            if (d.disk && ((L.y.th <= kHalfPi) != (y64n.th <= kHalfPi))) note_crossing<0, PREC>(L, L.y, sol);
             L.y = y64n;
             captured = y64n.r < d.r_capture;
             escaped = y64n.r > d.r_escape;
@@ -625,7 +715,7 @@ __device__ int step_ray32(Lane& L, StateF& yhi, const SolverDesc& sol) {
             const float pi2h = 1.57079637f, pi2l = -4.37113883e-08f;
             const bool s0 = !pair_below(pi2h, pi2l, yhi.th, L.lo.th);     // theta <= pi/2 before
             const bool s1 = !pair_below(pi2h, pi2l, hi.th, lo.th);        // and after
-            if (d.disk && s0 != s1) note_crossing<0>(L, pair_to64(yhi, L.lo), sol);
+            if (d.disk && s0 != s1) note_crossing<0, PREC>(L, pair_to64(yhi, L.lo), sol);
             yhi = hi;
             L.lo = lo;
             captured = pair_below(hi.r, lo.r, L.caph, L.capl);
@@ -688,7 +778,7 @@ __device__ __forceinline__ void trace_loop(const ImageDesc* descs, int n_desc, l
         const int n_free = __popc(__ballot_sync(kFull, st != kRun));
         if (n_free > 0 && (n_free >= tp.refill || n_free == 32) &&
             (!drained || __any_sync(kFull, st == kDone))) {
-            if (st != kIdle && L.pend) refine_pending<METRIC>(L, sol);
+            if (st != kIdle && L.pend) refine_pending<METRIC, PREC>(L, sol);
             if (st == kDone) {
                 if (PREC != 0) check_h64<ACC>(L, yhi);
                 write_final(L, L.code);
@@ -722,7 +812,7 @@ __device__ __forceinline__ void trace_loop(const ImageDesc* descs, int n_desc, l
         // ---- step phases ---------------------------------------------------
         if (PREC == 0) {
             if (st == kRun) {
-                const int code = step_ray64<METRIC>(L, sol);
+                const int code = step_ray64<METRIC, 0>(L, sol);
                 if (code >= 0) {
                     L.code = code;
                     st = kDone;
@@ -749,7 +839,7 @@ __device__ __forceinline__ void trace_loop(const ImageDesc* descs, int n_desc, l
                     }
                     L.k32_ok = false;
                     L.h = (double)L.hf;
-                    const int code = step_ray64<0>(L, sol);
+                    const int code = step_ray64<0, PREC>(L, sol);
                     L.hf = (float)L.h;
                     if (ACC == 1) split_state(L.y, yhi, L.lo);
                     if (code >= 0) {
@@ -769,7 +859,7 @@ __device__ __forceinline__ void trace_loop(const ImageDesc* descs, int n_desc, l
         // ---- batched crossing refinement -----------------------------------
         const unsigned pend = __ballot_sync(kFull, st == kRun && L.pend);
         if (pend && __popc(pend) >= tp.crossing_batch) {
-            if (st == kRun && L.pend) refine_pending<METRIC>(L, sol);
+            if (st == kRun && L.pend) refine_pending<METRIC, PREC>(L, sol);
         }
         // ---- FP64 |H| monitor (mixed) --------------------------------------
         if (PREC != 0 && (iter % (unsigned)tp.monitor_period) == 0) {

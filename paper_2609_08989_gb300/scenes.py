@@ -27,7 +27,7 @@ from typing import List, Optional
 import numpy as np
 
 FP64, MIXED, MIXED_PAIR = 0, 1, 2
-REFINE_HENON, REFINE_HERMITE = 0, 1
+REFINE_HENON, REFINE_HERMITE, REFINE_HENON64 = 0, 1, 2
 METRIC_KERR, METRIC_TABLE = 0, 1
 
 

@@ -40,12 +40,14 @@ def ref256(orc):
     return sc, orc.trace(sc)
 
 
-@pytest.mark.parametrize("precision", [scenes.MIXED, scenes.MIXED_PAIR])
-@pytest.mark.parametrize("fp64_factor", [0.0, -1.0])
-def test_mixed_against_oracle(T, orc, ref256, precision, fp64_factor):
+@pytest.mark.parametrize("precision,fp64_factor,refine", [
+    (scenes.MIXED, 0.0, scenes.REFINE_HENON), (scenes.MIXED_PAIR, 0.0, scenes.REFINE_HENON),
+    (scenes.MIXED, -1.0, scenes.REFINE_HENON), (scenes.MIXED_PAIR, -1.0, scenes.REFINE_HENON),
+    (scenes.MIXED_PAIR, 0.0, scenes.REFINE_HENON64)])
+def test_mixed_against_oracle(T, orc, ref256, precision, fp64_factor, refine):
     base, ref = ref256
     sc = base.replace(precision=precision, rtol=scenes.MIXED_RTOL, atol=scenes.MIXED_RTOL,
-                      fp64_radius_factor=fp64_factor)
+                      fp64_radius_factor=fp64_factor, refine=refine)
     got = run(T, sc)
     bad = np.nonzero(got["code"] != ref["code"])[0]
     for q in bad:
