@@ -54,7 +54,7 @@ class Scene(C.Structure):
         ("beta_min", C.c_double), ("beta_max", C.c_double),
         ("rtol", C.c_double), ("atol", C.c_double), ("h0", C.c_double), ("h_min", C.c_double),
         ("max_steps", C.c_longlong), ("horizon_eps", C.c_double), ("escape_factor", C.c_double),
-        ("refine", C.c_int),
+        ("refine", C.c_int), ("method", C.c_int),
         ("disk_enabled", C.c_int), ("r_in", C.c_double), ("r_out", C.c_double), ("mdot", C.c_double),
         ("max_crossings", C.c_int), ("doppler", C.c_int),
     ]
@@ -99,6 +99,9 @@ def lib():
             L.orc_redshift.restype = C.c_double
             L.orc_dp5_step.argtypes = [C.c_int, _FN, C.c_void_p, _D, _D, C.c_double, _D, _D, _D]
             L.orc_dp5_tableau.argtypes = [_D, _D, _D, _D]
+            L.orc_rk_step.argtypes = [C.c_int, C.c_int, _FN, C.c_void_p, _D, _D, C.c_double, _D, _D, _D]
+            L.orc_rk_tableau.argtypes = [C.c_int, _D, _D, _D, _D]
+            L.orc_rk_tableau.restype = C.c_int
             i8 = C.POINTER(C.c_int8)
             i32 = C.POINTER(C.c_int32)
             L.orc_trace_ray.argtypes = [SP, C.c_double, C.c_double, C.c_int, _D, _D, _D,
@@ -256,14 +259,15 @@ def redshift(sc, r, p_t, p_phi):
     return lib().orc_redshift(C.byref(s), r, p_t, p_phi)
 
 
-def tableau():
+def tableau(method: int = 0):
+    """(c, A, b, bhat, stages) of a 5(4) pair: 0 Dormand-Prince, 1 Cash-Karp, 2 Fehlberg."""
     c, a, b, bh = np.zeros(7), np.zeros(49), np.zeros(7), np.zeros(7)
-    lib().orc_dp5_tableau(_dp(c), _dp(a), _dp(b), _dp(bh))
-    return c, a.reshape(7, 7), b, bh
+    st = lib().orc_rk_tableau(method, _dp(c), _dp(a), _dp(b), _dp(bh))
+    return c[:st], a.reshape(7, 7)[:st, :st], b[:st], bh[:st]
 
 
-def dp5_step(f, y, h):
-    """One Dormand-Prince 5(4) step of the oracle's generic stepper on dy/dx = f(y)."""
+def dp5_step(f, y, h, method: int = 0):
+    """One step of the oracle's generic 5(4) stepper (default Dormand-Prince) on dy/dx = f(y)."""
     y = np.ascontiguousarray(y, dtype=np.float64)
     n = len(y)
 
@@ -276,7 +280,7 @@ def dp5_step(f, y, h):
     fn = _FN(cb)
     f0 = np.asarray(f(y.copy()), dtype=np.float64)
     yn, fnew, err = np.zeros(n), np.zeros(n), np.zeros(n)
-    lib().orc_dp5_step(n, fn, None, _dp(y), _dp(f0), h, _dp(yn), _dp(fnew), _dp(err))
+    lib().orc_rk_step(method, n, fn, None, _dp(y), _dp(f0), h, _dp(yn), _dp(fnew), _dp(err))
     return yn, fnew, err
 
 

@@ -323,61 +323,126 @@ int orc_initial_state(const orc_scene *s, double alpha, double beta, double y[8]
 }
 
 /* ------------------------------------------------------------------------ */
-/* Dormand-Prince 5(4), Sec. 3.2 (Dormand & Prince 1980): seven stages with  */
-/* the first-same-as-last property; the fifth-order weights advance the       */
-/* solution and the difference to the embedded fourth-order weights is the   */
-/* error estimate.                                                           */
+/* Embedded Runge-Kutta 5(4) pairs of Sec. 3.2: Dormand-Prince (1980, seven    */
+/* stages, first-same-as-last), Cash-Karp (1990) and Fehlberg (1969, six     */
+/* stages each).  In all three the fifth-order weights advance the solution   */
+/* (local extrapolation) and the difference to the embedded fourth-order      */
+/* weights is the error estimate.                                             */
 /* ------------------------------------------------------------------------ */
 
-static const double DP_C[7] = { 0.0, 1.0 / 5.0, 3.0 / 10.0, 4.0 / 5.0, 8.0 / 9.0, 1.0, 1.0 };
-static const double DP_A[7][6] = {
-    { 0, 0, 0, 0, 0, 0 },
-    { 1.0 / 5.0, 0, 0, 0, 0, 0 },
-    { 3.0 / 40.0, 9.0 / 40.0, 0, 0, 0, 0 },
-    { 44.0 / 45.0, -56.0 / 15.0, 32.0 / 9.0, 0, 0, 0 },
-    { 19372.0 / 6561.0, -25360.0 / 2187.0, 64448.0 / 6561.0, -212.0 / 729.0, 0, 0 },
-    { 9017.0 / 3168.0, -355.0 / 33.0, 46732.0 / 5247.0, 49.0 / 176.0, -5103.0 / 18656.0, 0 },
-    { 35.0 / 384.0, 0.0, 500.0 / 1113.0, 125.0 / 192.0, -2187.0 / 6784.0, 11.0 / 84.0 },
+typedef struct {
+    int stages;          /* number of stages */
+    int fsal;            /* the last stage sits at the new solution */
+    double c[7], a[7][6], b[7], bhat[7];
+} rk_tableau;
+
+static const rk_tableau TAB_DP = {
+    7, 1,
+    { 0.0, 1.0 / 5.0, 3.0 / 10.0, 4.0 / 5.0, 8.0 / 9.0, 1.0, 1.0 },
+    { { 0, 0, 0, 0, 0, 0 },
+      { 1.0 / 5.0, 0, 0, 0, 0, 0 },
+      { 3.0 / 40.0, 9.0 / 40.0, 0, 0, 0, 0 },
+      { 44.0 / 45.0, -56.0 / 15.0, 32.0 / 9.0, 0, 0, 0 },
+      { 19372.0 / 6561.0, -25360.0 / 2187.0, 64448.0 / 6561.0, -212.0 / 729.0, 0, 0 },
+      { 9017.0 / 3168.0, -355.0 / 33.0, 46732.0 / 5247.0, 49.0 / 176.0, -5103.0 / 18656.0, 0 },
+      { 35.0 / 384.0, 0.0, 500.0 / 1113.0, 125.0 / 192.0, -2187.0 / 6784.0, 11.0 / 84.0 } },
+    { 35.0 / 384.0, 0.0, 500.0 / 1113.0, 125.0 / 192.0, -2187.0 / 6784.0, 11.0 / 84.0, 0.0 },
+    { 5179.0 / 57600.0, 0.0, 7571.0 / 16695.0, 393.0 / 640.0, -92097.0 / 339200.0, 187.0 / 2100.0, 1.0 / 40.0 },
 };
-static const double DP_B[7] = { 35.0 / 384.0, 0.0, 500.0 / 1113.0, 125.0 / 192.0,
-                                -2187.0 / 6784.0, 11.0 / 84.0, 0.0 };
-static const double DP_BHAT[7] = { 5179.0 / 57600.0, 0.0, 7571.0 / 16695.0, 393.0 / 640.0,
-                                   -92097.0 / 339200.0, 187.0 / 2100.0, 1.0 / 40.0 };
+
+static const rk_tableau TAB_CK = {
+    6, 0,
+    { 0.0, 1.0 / 5.0, 3.0 / 10.0, 3.0 / 5.0, 1.0, 7.0 / 8.0, 0.0 },
+    { { 0, 0, 0, 0, 0, 0 },
+      { 1.0 / 5.0, 0, 0, 0, 0, 0 },
+      { 3.0 / 40.0, 9.0 / 40.0, 0, 0, 0, 0 },
+      { 3.0 / 10.0, -9.0 / 10.0, 6.0 / 5.0, 0, 0, 0 },
+      { -11.0 / 54.0, 5.0 / 2.0, -70.0 / 27.0, 35.0 / 27.0, 0, 0 },
+      { 1631.0 / 55296.0, 175.0 / 512.0, 575.0 / 13824.0, 44275.0 / 110592.0, 253.0 / 4096.0, 0 },
+      { 0, 0, 0, 0, 0, 0 } },
+    { 37.0 / 378.0, 0.0, 250.0 / 621.0, 125.0 / 594.0, 0.0, 512.0 / 1771.0, 0.0 },
+    { 2825.0 / 27648.0, 0.0, 18575.0 / 48384.0, 13525.0 / 55296.0, 277.0 / 14336.0, 1.0 / 4.0, 0.0 },
+};
+
+static const rk_tableau TAB_F = {
+    6, 0,
+    { 0.0, 1.0 / 4.0, 3.0 / 8.0, 12.0 / 13.0, 1.0, 1.0 / 2.0, 0.0 },
+    { { 0, 0, 0, 0, 0, 0 },
+      { 1.0 / 4.0, 0, 0, 0, 0, 0 },
+      { 3.0 / 32.0, 9.0 / 32.0, 0, 0, 0, 0 },
+      { 1932.0 / 2197.0, -7200.0 / 2197.0, 7296.0 / 2197.0, 0, 0, 0 },
+      { 439.0 / 216.0, -8.0, 3680.0 / 513.0, -845.0 / 4104.0, 0, 0 },
+      { -8.0 / 27.0, 2.0, -3544.0 / 2565.0, 1859.0 / 4104.0, -11.0 / 40.0, 0 },
+      { 0, 0, 0, 0, 0, 0 } },
+    { 16.0 / 135.0, 0.0, 6656.0 / 12825.0, 28561.0 / 56430.0, -9.0 / 50.0, 2.0 / 55.0, 0.0 },
+    { 25.0 / 216.0, 0.0, 1408.0 / 2565.0, 2197.0 / 4104.0, -1.0 / 5.0, 0.0, 0.0 },
+};
+
+/* method: 0 Dormand-Prince, 1 Cash-Karp, 2 Fehlberg */
+static const rk_tableau *tableau_of(int method)
+{
+    return method == 1 ? &TAB_CK : (method == 2 ? &TAB_F : &TAB_DP);
+}
+
+int orc_rk_tableau(int method, double c[7], double a[49], double b[7], double bhat[7])
+{
+    const rk_tableau *t = tableau_of(method);
+    for (int i = 0; i < 7; ++i) {
+        c[i] = t->c[i];
+        b[i] = t->b[i];
+        bhat[i] = t->bhat[i];
+        for (int j = 0; j < 7; ++j) a[i * 7 + j] = (j < 6) ? t->a[i][j] : 0.0;
+    }
+    return t->stages;
+}
 
 void orc_dp5_tableau(double c[7], double a[49], double b[7], double bhat[7])
 {
-    for (int i = 0; i < 7; ++i) {
-        c[i] = DP_C[i];
-        b[i] = DP_B[i];
-        bhat[i] = DP_BHAT[i];
-        for (int j = 0; j < 7; ++j) a[i * 7 + j] = (j < 6) ? DP_A[i][j] : 0.0;
-    }
+    orc_rk_tableau(0, c, a, b, bhat);
 }
 
 #define ORC_NMAX 8
 
-/* One step of size h from (y, f0 = f(y)).  ynew is the fifth-order solution
- * (the stage-7 point), fnew = f(ynew), err = ynew - yhat (fourth order). */
-void orc_dp5_step(int n, orc_fn f, void *ctx, const double *y, const double *f0,
-                  double h, double *ynew, double *fnew, double *err)
+/* One step of size h from (y, f0 = f(y)).  ynew is the fifth-order solution,
+ * fnew = f(ynew) (the last stage itself for Dormand-Prince, an extra
+ * evaluation otherwise), err = ynew - yhat (fourth order). */
+void orc_rk_step(int method, int n, orc_fn f, void *ctx, const double *y, const double *f0,
+                 double h, double *ynew, double *fnew, double *err)
 {
+    const rk_tableau *t = tableau_of(method);
     double k[7][ORC_NMAX], ys[ORC_NMAX];
     for (int i = 0; i < n; ++i) k[0][i] = f0[i];
-    for (int st = 1; st < 7; ++st) {
+    for (int st = 1; st < t->stages; ++st) {
         for (int i = 0; i < n; ++i) {
             double acc = 0.0;
-            for (int j = 0; j < st; ++j) acc += DP_A[st][j] * k[j][i];
+            for (int j = 0; j < st; ++j) acc += t->a[st][j] * k[j][i];
             ys[i] = y[i] + h * acc;
         }
         f(ctx, ys, k[st]);
     }
     for (int i = 0; i < n; ++i) {
-        ynew[i] = ys[i];                 /* stage 7 sits at the fifth-order solution */
-        fnew[i] = k[6][i];
+        if (t->fsal) {
+            ynew[i] = ys[i];             /* the last stage sits at the fifth-order solution */
+        } else {
+            double acc = 0.0;
+            for (int j = 0; j < t->stages; ++j) acc += t->b[j] * k[j][i];
+            ynew[i] = y[i] + h * acc;
+        }
         double e = 0.0;
-        for (int j = 0; j < 7; ++j) e += (DP_B[j] - DP_BHAT[j]) * k[j][i];
+        for (int j = 0; j < t->stages; ++j) e += (t->b[j] - t->bhat[j]) * k[j][i];
         err[i] = h * e;
     }
+    if (t->fsal) {
+        for (int i = 0; i < n; ++i) fnew[i] = k[t->stages - 1][i];
+    } else {
+        f(ctx, ynew, fnew);
+    }
+}
+
+void orc_dp5_step(int n, orc_fn f, void *ctx, const double *y, const double *f0,
+                  double h, double *ynew, double *fnew, double *err)
+{
+    orc_rk_step(0, n, f, ctx, y, f0, h, ynew, fnew, err);
 }
 
 /* Reading (error norm): Hairer's mean-square norm over the dynamical
@@ -516,7 +581,7 @@ static void rhs_in_theta(void *ctx, const double *y, double *dy)
 
 /* Reading (refinement, default): Henon's exact-step method (M. Henon, Physica D
  * 5, 412, 1982).  From the start of the accepted step, integrate the system in
- * theta with Dormand-Prince 5(4) over Delta theta = pi/2 - theta_k, in 2^m equal
+ * theta with the ray's 5(4) pair over Delta theta = pi/2 - theta_k, in 2^m equal
  * sub-steps, m = 0, 1, ... up to 6, taking the first m whose largest sub-step
  * error norm (over r, p_r, p_theta) is <= 1.  The main step sequence is not
  * changed. */
@@ -535,7 +600,7 @@ static double refine_henon(const orc_scene *s, const double *y0, const double *f
         }
         double worst = 0.0;
         for (int q = 0; q < nsub; ++q) {
-            orc_dp5_step(8, rhs_in_theta, &ctx, z, gz, dl, zn, gn, e);
+            orc_rk_step(s->method, 8, rhs_in_theta, &ctx, z, gz, dl, zn, gn, e);
             double e2 = err_norm2(s, z, zn, e, idx3, 3);
             if (!(e2 <= worst)) worst = e2;     /* NaN-propagating max */
             memcpy(z, zn, sizeof z);
@@ -633,7 +698,7 @@ static void trace_one(const orc_scene *s, const scene_consts *c, double alpha, d
             res->code = ORC_UNDERFLOW;
             break;
         }
-        orc_dp5_step(8, rhs_cb, (void *)s, y, f, h, yn, fn, e);
+        orc_rk_step(s->method, 8, rhs_cb, (void *)s, y, f, h, yn, fn, e);
         double err2 = err_norm2(s, y, yn, e, NORM_IDX, 4);
         if (isnan(err2) || !all_finite(yn, 8)) {
             res->code = ORC_NONFINITE;

@@ -57,6 +57,7 @@ typedef struct {
     double horizon_eps;      /* captured when r < r_h (1 + eps) */
     double escape_factor;    /* escaped when r > factor * r_obs */
     int    refine;           /* 0 = Henon exact-step, 1 = cubic-Hermite + bisection */
+    int    method;           /* 0 = Dormand-Prince, 1 = Cash-Karp, 2 = Fehlberg (5(4) pairs) */
     /* disk (Sec. 2.3-2.4) */
     int    disk_enabled;
     double r_in;             /* <= 0: prograde ISCO of (M, a) */
@@ -96,8 +97,11 @@ double orc_isco(double M, double a);
 double orc_flux(double M, double a, double mdot, double r);
 double orc_redshift(const orc_scene *s, double r, double p_t, double p_phi);
 
-/* ---- Dormand-Prince 5(4) on a generic system (exported for the order pins) ---- */
+/* ---- embedded 5(4) pairs on a generic system (exported for the order pins) ---- */
 typedef void (*orc_fn)(void *ctx, const double *y, double *dy);
+void orc_rk_step(int method, int n, orc_fn f, void *ctx, const double *y, const double *f0,
+                 double h, double *ynew, double *fnew, double *err);
+int  orc_rk_tableau(int method, double c[7], double a[49], double b[7], double bhat[7]);
 void orc_dp5_step(int n, orc_fn f, void *ctx, const double *y, const double *f0,
                   double h, double *ynew, double *fnew, double *err);
 void orc_dp5_tableau(double c[7], double a[49], double b[7], double bhat[7]);

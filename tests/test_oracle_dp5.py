@@ -1,6 +1,7 @@
-"""Pins for the oracle's Dormand-Prince 5(4) pair: the Butcher order conditions
-(so a mistyped coefficient fails), the local orders of the solution and of the
-error estimate, and the global order on a harmonic oscillator."""
+"""Pins for the oracle's embedded 5(4) pairs (Dormand-Prince, Cash-Karp,
+Fehlberg; Sec. 3.2): the Butcher order conditions (so a mistyped coefficient
+fails), the local orders of the solution and of the error estimate, and the
+global order on a harmonic oscillator."""
 from fractions import Fraction as Fr
 import itertools
 
@@ -12,13 +13,18 @@ def _frac(x):
     return Fr(x).limit_denominator(10 ** 7)
 
 
-def test_order_conditions(orc):
-    c, A, b, bh = orc.tableau()
+METHODS = [0, 1, 2]      # Dormand-Prince, Cash-Karp, Fehlberg
+
+
+@pytest.mark.parametrize("method", METHODS)
+def test_order_conditions(orc, method):
+    c, A, b, bh = orc.tableau(method)
     c = [_frac(x) for x in c]
     A = [[_frac(x) for x in row] for row in A]
     b = [_frac(x) for x in b]
     bh = [_frac(x) for x in bh]
-    s = 7
+    s = len(c)
+    assert s == (7 if method == 0 else 6)
     # row-sum condition and explicitness
     for i in range(s):
         assert sum(A[i]) == c[i]
@@ -52,11 +58,31 @@ def test_order_conditions(orc):
         assert got == want
     # the embedded pair really differs at order 5
     assert any(g != w for g, w in conds(bh)[8:])
-    # first-same-as-last: the last stage is evaluated at the solution
-    assert A[6][:6] == b[:6] and b[6] == 0 and c[6] == 1
+    if method == 0:
+        # first-same-as-last: the last stage is evaluated at the solution
+        assert A[6][:6] == b[:6] and b[6] == 0 and c[6] == 1
 
 
-def test_local_orders(orc):
+def test_tableau_values(orc):
+    """A few coefficients as printed by the pairs' authors (Cash & Karp 1990,
+    Fehlberg 1969), beyond what the order conditions fix."""
+    c, A, b, bh = orc.tableau(1)
+    assert _frac(c[5]) == Fr(7, 8) and _frac(A[5][3]) == Fr(44275, 110592)
+    assert _frac(b[5]) == Fr(512, 1771) and _frac(bh[4]) == Fr(277, 14336)
+    c, A, b, bh = orc.tableau(2)
+    assert _frac(c[3]) == Fr(12, 13) and _frac(A[3][1]) == Fr(-7200, 2197)
+    assert _frac(b[3]) == Fr(28561, 56430) and _frac(bh[4]) == Fr(-1, 5)
+
+
+@pytest.mark.parametrize("method", METHODS)
+def test_fnew_is_rhs_at_solution(orc, method):
+    f = lambda y: [y[1], -y[0] + 0.1 * y[0] ** 3]
+    yn, fn, _ = orc.dp5_step(f, np.array([0.3, -0.2]), 0.07, method)
+    assert np.allclose(fn, f(yn), rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("method", METHODS)
+def test_local_orders(orc, method):
     lam = -0.7 + 0.3j
 
     def f(y):
@@ -65,7 +91,7 @@ def test_local_orders(orc):
 
     errs, ests = [], []
     for h in (0.2, 0.1, 0.05):
-        yn, _, e = orc.dp5_step(f, np.array([1.0, 0.0]), h)
+        yn, _, e = orc.dp5_step(f, np.array([1.0, 0.0]), h, method)
         ex = np.exp(lam * h)
         errs.append(abs(complex(*yn) - ex))
         ests.append(abs(complex(*e)))
@@ -75,14 +101,15 @@ def test_local_orders(orc):
         assert 2 ** 4.6 < ests[k] / ests[k + 1] < 2 ** 5.4
 
 
-def test_global_order_harmonic_oscillator(orc):
+@pytest.mark.parametrize("method", METHODS)
+def test_global_order_harmonic_oscillator(orc, method):
     f = lambda y: [y[1], -y[0]]
     res = []
     for n in (20, 40, 80):
         h = 2 * np.pi / n
         y = np.array([1.0, 0.0])
         for _ in range(n):
-            y, _, _ = orc.dp5_step(f, y, h)
+            y, _, _ = orc.dp5_step(f, y, h, method)
         res.append(np.hypot(y[0] - 1.0, y[1]))
     for k in range(2):
         order = np.log2(res[k] / res[k + 1])
