@@ -35,6 +35,12 @@ FP64_PEAK_TFLOPS = SM_COUNT * SM_MAX_MHZ * 1e6 * 2 * 2 / 1e12
 # counted from the kernel source (FMA = 2, add/mul/div/rcp/sqrt = 1, sin and cos 1 each):
 # 6 flow evaluations x 65 + stage combinations 232 + error norm 20 + step control 5.
 FLOPS_PER_STEP = 6 * 65 + 232 + 20 + 5
+# Cash-Karp and Fehlberg also evaluate the flow six times per step attempt (five
+# stages and the new point); their stage sums have one (Fehlberg: e_7 = 0) or two
+# (Cash-Karp: b_5 = e_7 = 0) fewer FMA per state component.
+FLOPS_PER_STEP_METHOD = {0: FLOPS_PER_STEP, 1: FLOPS_PER_STEP - 2 * 2 * 4, 2: FLOPS_PER_STEP - 2 * 4}
+METHODS = {"dopri5": 0, "cash_karp": 1, "fehlberg": 2}
+METHOD_NAMES = {v: k for k, v in METHODS.items()}
 # The same count for an FP32 step of the mixed paths (the rearranged FP32 flow is 72).
 FLOPS_PER_STEP_F32 = 6 * 72 + 232 + 20 + 5
 FP32_PEAK_TFLOPS = SM_COUNT * SM_MAX_MHZ * 1e6 * 128 * 2 / 1e12
@@ -58,6 +64,10 @@ def parse():
     p.add_argument("--precision", default="fp64", choices=["fp64", "mixed", "mixed_pair"],
                    help="path of the main measurement (default: the FP64 headline)")
     p.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision objects")
+    p.add_argument("--method", default="dopri5", choices=list(METHODS),
+                   help="5(4) pair of the FP64 run (default: Dormand-Prince, the headline)")
+    p.add_argument("--no-pairs", action="store_true",
+                   help="skip the Cash-Karp / Fehlberg objects of the default line")
     p.add_argument("--workload", default="kerr_disk", choices=["kerr_disk", "batch", "table"],
                    help="kerr_disk: the 1024^2 headline image (default); batch: 64 uneven images in one "
                         "persistent launch, replayed from a CUDA graph; table: the 4096^2 tabulated-metric image")
@@ -74,10 +84,12 @@ def dist_env():
 PRECISIONS = {"fp64": 0, "mixed": 1, "mixed_pair": 2}
 
 
-def workload(n, precision="fp64"):
+def workload(n, precision="fp64", method="dopri5"):
     from paper_2609_08989_gb300 import scenes
     if precision == "fp64":
-        return scenes.kerr_disk(n)
+        return scenes.kerr_disk(n).replace(method=METHODS[method])
+    if method != "dopri5":
+        raise SystemExit("the mixed-precision paths step with Dormand-Prince only")
     return scenes.kerr_disk_mixed(n).replace(precision=PRECISIONS[precision])
 
 
@@ -105,7 +117,7 @@ def time_variant(T, sc, steps, warmup, flush, tune=None):
 def config_dict(sc, world):
     return {"workload": sc.name, "nx": sc.nx, "ny": sc.ny, "a": sc.a, "theta_obs_deg": 60.0,
             "r_obs": sc.r_obs, "field": [sc.alpha_min, sc.alpha_max], "rtol": sc.rtol, "atol": sc.atol,
-            "integrator": "dopri5", "disk": [ "isco", sc.r_out], "max_crossings": sc.max_crossings,
+            "integrator": METHOD_NAMES[sc.method], "disk": ["isco", sc.r_out], "max_crossings": sc.max_crossings,
             "global_batch": sc.npix * world, "per_gpu_rays": sc.npix, "parallelism": "dp%d" % world,
             "l2": "flushed between timed steps (256 MiB write); working set is a few MB of state + outputs"}
 
@@ -226,7 +238,7 @@ def run_tartarus(args):
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    sc = workload(args.n, args.precision)
+    sc = workload(args.n, args.precision, args.method)
     T.lib()
     out = T.alloc_outputs(sc.npix)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
@@ -302,8 +314,22 @@ def run_tartarus(args):
                            "h_max_escaped_p99": float(np.percentile(h[esc], 99)) if esc.any() else None,
                            "h_max_captured": float(h[~esc].max()) if (~esc).any() else None,
                            "rk_step_attempts_per_image": int(mout["steps"].sum().item() + mout["rejects"].sum().item())}
+    pairs = {}
+    if not args.no_pairs and args.precision == "fp64" and args.method == "dopri5":
+        # the other two 5(4) pairs of Sec. 3.2 on the same image, same tolerance
+        for name in ("cash_karp", "fehlberg"):
+            psc = workload(args.n, "fp64", name)
+            ms, pout = time_variant(T, psc, max(2, args.steps // 2), 1, flush)
+            h = pout["h_max"].cpu().numpy()
+            esc = pout["code"].cpu().numpy() == 0
+            att = int(pout["steps"].sum().item() + pout["rejects"].sum().item())
+            pach = FLOPS_PER_STEP_METHOD[psc.method] * att / (ms / 1e3) / 1e12
+            pairs[name] = {"value": psc.npix / (ms / 1e3), "unit": UNIT, "ms_per_image": ms,
+                           "rk_step_attempts_per_image": att,
+                           "h_max_escaped": float(h[esc].max()) if esc.any() else None,
+                           "fp64_tflops": pach, "frac": pach / FP64_PEAK_TFLOPS}
     if rank == 0:
-        flops = FLOPS_PER_STEP * step_attempts
+        flops = FLOPS_PER_STEP_METHOD[sc.method] * step_attempts
         achieved = flops / (mean_kern / 1e3) / 1e12
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -314,11 +340,14 @@ def run_tartarus(args):
             "rk_step_attempts_per_image": step_attempts,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                          "frac": achieved / FP64_PEAK_TFLOPS,
-                         "traffic": TRAFFIC_BYTES_PER_RAY * sc.npix if args.precision == "fp64" else None,
+                         "traffic": (TRAFFIC_BYTES_PER_RAY * sc.npix
+                                     if args.precision == "fp64" and sc.method == 0 else None),
                          "traffic_note": "bytes per launch, scaled from a 256^2 ncu capture by rays",
-                         "kernel": "trace_kernel64_b256<0,1>", "kernel_ms": mean_kern,
+                         "kernel": ("trace_kernel64_b256<0,1>" if sc.method == 0
+                                    else "trace_kernel_rk<%d,0,1,256>" % sc.method), "kernel_ms": mean_kern,
                          "peak_source": "FP64 pipe: 152 SMs x 2070 MHz x 2 DFMA/clk (derived)",
-                         "flops_per_unit": FLOPS_PER_STEP, "unit_of_work": "Dormand-Prince step attempt"},
+                         "flops_per_unit": FLOPS_PER_STEP_METHOD[sc.method],
+                         "unit_of_work": "%s step attempt" % METHOD_NAMES[sc.method]},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": DESC_BYTES,
                     "d2h_bytes_per_step": BYTES_OUT_PER_PIXEL * sc.npix},
             "gpu_launches": launches,
@@ -328,6 +357,8 @@ def run_tartarus(args):
             line["dtype"] = "f32 stages / f64 state" if args.precision == "mixed" else "f32 stages / f32-pair state"
             line["roofline"] = None          # the FP64 flop count does not describe the mixed step
         line.update(mixed)
+        if pairs:
+            line["pairs"] = pairs
         if not args.no_cpu_baseline:
             v, rays, cores, tsec = time_oracle(sc, args.cpu_seconds)
             line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",

@@ -62,6 +62,8 @@ extern "C" {
 #define TT_METRIC_KERR   0
 #define TT_METRIC_TABLE  1
 #define TT_DP54          0   /* Dormand-Prince 5(4) (paper Sec. 3.2)   */
+#define TT_CK45          1   /* Cash-Karp 5(4) (paper Sec. 3.2), FP64 only */
+#define TT_F45           2   /* Fehlberg 5(4) (paper Sec. 3.2), FP64 only  */
 #define TT_FP64          0   /* all arithmetic in binary64             */
 #define TT_MIXED         1   /* FP32 stages, FP64 state accumulation   */
 #define TT_MIXED_PAIR    2   /* FP32 stages, compensated FP32-pair state accumulation (~48 bits) */
@@ -105,10 +107,17 @@ typedef struct {
  * with a table they return TT_EUNSUPPORTED.  On the mixed paths h_max is the
  * largest |H| evaluated in FP64: at the start, at every FP64 step, at the
  * start of every step with a disk crossing, every monitor_period warp
- * iterations and at the end. */
+ * iterations and at the end.
+ * method: the embedded 5(4) pair of Sec. 3.2; each propagates its fifth-order
+ * solution and takes the difference to its fourth-order one as the error
+ * estimate.  TT_CK45 and TT_F45 run in FP64 only (other precisions return
+ * TT_EUNSUPPORTED), for either metric kind, but a batch that mixes closed-form
+ * Kerr and tabulated images returns TT_EUNSUPPORTED for them, with nothing
+ * launched; other methods give TT_EINVAL.  tt_tune.reg_variant applies to
+ * TT_DP54 only. */
 typedef struct {
-    int method;                 /* TT_DP54 */
-    int precision;              /* TT_FP64 or TT_MIXED */
+    int method;                 /* TT_DP54, TT_CK45 or TT_F45 */
+    int precision;              /* TT_FP64, TT_MIXED or TT_MIXED_PAIR */
     double rtol, atol, h0, h_min;
     long long max_steps;
     double horizon_eps, escape_factor;

@@ -56,8 +56,9 @@ int check_metric(const tt_metric* m) {
 
 int check_solver(const tt_solver* s) {
     if (!s) return TT_EINVAL;
-    if (s->method != TT_DP54) return TT_EUNSUPPORTED;
+    if (s->method != TT_DP54 && s->method != TT_CK45 && s->method != TT_F45) return TT_EINVAL;
     if (s->precision != TT_FP64 && s->precision != TT_MIXED && s->precision != TT_MIXED_PAIR) return TT_EINVAL;
+    if (s->method != TT_DP54 && s->precision != TT_FP64) return TT_EUNSUPPORTED;
     if (!is_finite(s->rtol) || !is_finite(s->atol) || !(s->rtol > 0.0) || !(s->atol > 0.0)) return TT_EINVAL;
     if (!is_finite(s->h0) || !is_finite(s->h_min)) return TT_EINVAL;
     if (s->max_steps < 1) return TT_EINVAL;
@@ -204,6 +205,7 @@ tt::SolverDesc make_solver(const tt_solver* s) {
     sd.max_steps = s->max_steps;
     sd.refine = s->refine;
     sd.precision = s->precision;
+    sd.method = s->method;
     return sd;
 }
 
@@ -234,6 +236,18 @@ int check_shape(const tt_tune* t) {
     if (t->fp64_batch < 0 || t->fp64_batch > 32) return TT_EINVAL;
     if (t->monitor_period < 0 || t->fp64_wait < 0) return TT_EINVAL;
     return TT_OK;
+}
+
+// The Cash-Karp and Fehlberg kernels take one metric kind per launch: a batch
+// with both closed-form Kerr and tabulated images is refused for them.
+int check_kinds(const tt_image* images, int n, const tt_solver* s) {
+    if (s->method == TT_DP54) return TT_OK;
+    bool kerr = false, table = false;
+    for (int i = 0; i < n; ++i) {
+        if (images[i].metric.kind == TT_METRIC_TABLE) table = true;
+        else kerr = true;
+    }
+    return (kerr && table) ? TT_EUNSUPPORTED : TT_OK;
 }
 
 // Work-queue counters: one small device array per device, allocated on the
@@ -351,6 +365,8 @@ int tartarus_trace_batch_noalloc(const tt_image* images, int n, const tt_solver*
     int rc = check_solver(solver);
     if (rc) return rc;
     rc = check_shape(tune);
+    if (rc) return rc;
+    rc = check_kinds(images, n, solver);
     if (rc) return rc;
     unsigned long long* scratch = nullptr;
     rc = noalloc_scratch(&scratch);
@@ -472,6 +488,8 @@ int tartarus_trace_batch(const tt_image* images, int n, const tt_solver* solver,
     int rc = check_solver(solver);
     if (rc) return rc;
     rc = check_shape(tune);
+    if (rc) return rc;
+    rc = check_kinds(images, n, solver);
     if (rc) return rc;
     std::vector<tt::ImageDesc> descs;
     descs.reserve(n);

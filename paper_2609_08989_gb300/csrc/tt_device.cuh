@@ -382,4 +382,58 @@ constexpr double e6 = 11.0 / 84.0 - 187.0 / 2100.0;
 constexpr double e7 = -1.0 / 40.0;
 }  // namespace dp
 
+// Embedded 5(4) pairs of Sec. 3.2 for the FP64 stepper: stage nodes c_i,
+// coefficients a_ij, fifth-order weights b_i (they advance the solution) and
+// e_i = b_i - bhat_i (the error estimate).  b_2 = 0 and e_2 = 0 in all three.
+// Dormand-Prince has seven stages, the seventh at the new point (first same as
+// last, e_7 != 0); Cash-Karp and Fehlberg have six, and the flow at the new
+// point is one extra evaluation that becomes the next step's first stage.
+template <int METHOD>
+struct RK;
+
+template <>
+struct RK<0> {   // Dormand & Prince (1980)
+    static constexpr double c2 = dp::c2, c3 = dp::c3, c4 = dp::c4, c5 = dp::c5, c6 = 1.0;
+    static constexpr double a21 = dp::a21, a31 = dp::a31, a32 = dp::a32, a41 = dp::a41, a42 = dp::a42,
+                            a43 = dp::a43, a51 = dp::a51, a52 = dp::a52, a53 = dp::a53, a54 = dp::a54,
+                            a61 = dp::a61, a62 = dp::a62, a63 = dp::a63, a64 = dp::a64, a65 = dp::a65;
+    static constexpr double b1 = dp::b1, b3 = dp::b3, b4 = dp::b4, b5 = dp::b5, b6 = dp::b6;
+    static constexpr double e1 = dp::e1, e3 = dp::e3, e4 = dp::e4, e5 = dp::e5, e6 = dp::e6, e7 = dp::e7;
+};
+
+template <>
+struct RK<1> {   // Cash & Karp (1990)
+    static constexpr double c2 = 1.0 / 5.0, c3 = 3.0 / 10.0, c4 = 3.0 / 5.0, c5 = 1.0, c6 = 7.0 / 8.0;
+    static constexpr double a21 = 1.0 / 5.0;
+    static constexpr double a31 = 3.0 / 40.0, a32 = 9.0 / 40.0;
+    static constexpr double a41 = 3.0 / 10.0, a42 = -9.0 / 10.0, a43 = 6.0 / 5.0;
+    static constexpr double a51 = -11.0 / 54.0, a52 = 5.0 / 2.0, a53 = -70.0 / 27.0, a54 = 35.0 / 27.0;
+    static constexpr double a61 = 1631.0 / 55296.0, a62 = 175.0 / 512.0, a63 = 575.0 / 13824.0,
+                            a64 = 44275.0 / 110592.0, a65 = 253.0 / 4096.0;
+    static constexpr double b1 = 37.0 / 378.0, b3 = 250.0 / 621.0, b4 = 125.0 / 594.0, b5 = 0.0,
+                            b6 = 512.0 / 1771.0;
+    static constexpr double e1 = 37.0 / 378.0 - 2825.0 / 27648.0, e3 = 250.0 / 621.0 - 18575.0 / 48384.0,
+                            e4 = 125.0 / 594.0 - 13525.0 / 55296.0, e5 = -277.0 / 14336.0,
+                            e6 = 512.0 / 1771.0 - 1.0 / 4.0, e7 = 0.0;
+};
+
+template <>
+struct RK<2> {   // Fehlberg (1969)
+    static constexpr double c2 = 1.0 / 4.0, c3 = 3.0 / 8.0, c4 = 12.0 / 13.0, c5 = 1.0, c6 = 1.0 / 2.0;
+    static constexpr double a21 = 1.0 / 4.0;
+    static constexpr double a31 = 3.0 / 32.0, a32 = 9.0 / 32.0;
+    static constexpr double a41 = 1932.0 / 2197.0, a42 = -7200.0 / 2197.0, a43 = 7296.0 / 2197.0;
+    static constexpr double a51 = 439.0 / 216.0, a52 = -8.0, a53 = 3680.0 / 513.0, a54 = -845.0 / 4104.0;
+    static constexpr double a61 = -8.0 / 27.0, a62 = 2.0, a63 = -3544.0 / 2565.0, a64 = 1859.0 / 4104.0,
+                            a65 = -11.0 / 40.0;
+    static constexpr double b1 = 16.0 / 135.0, b3 = 6656.0 / 12825.0, b4 = 28561.0 / 56430.0, b5 = -9.0 / 50.0,
+                            b6 = 2.0 / 55.0;
+    static constexpr double e1 = 16.0 / 135.0 - 25.0 / 216.0, e3 = 6656.0 / 12825.0 - 1408.0 / 2565.0,
+                            e4 = 28561.0 / 56430.0 - 2197.0 / 4104.0, e5 = -9.0 / 50.0 + 1.0 / 5.0,
+                            e6 = 2.0 / 55.0, e7 = 0.0;
+};
+
+// acc + w k, with the term dropped at compile time when the weight w is zero
+#define TT_MAC(w, k, acc) (((w) == 0.0) ? (acc) : fma((w), (k), (acc)))
+
 }  // namespace tt

@@ -64,6 +64,7 @@ struct SolverDesc {
     long long max_steps;
     int refine;                   // 0 Henon, 1 Hermite, 2 Henon in FP64 on the mixed paths too
     int precision;                // 0 FP64, 1 mixed (FP64 state), 2 mixed (FP32-pair state)
+    int method;                   // 0 Dormand-Prince, 1 Cash-Karp, 2 Fehlberg (FP64 only)
 };
 
 struct LaunchShape {
@@ -101,6 +102,12 @@ struct LaunchParams {
 };
 
 // Enqueue the persistent tracing kernel over n <= kMaxImagesPerLaunch images.
+// FP64 kernels of the Cash-Karp (METHOD 1) and Fehlberg (METHOD 2) pairs for
+// metric_mode 0 or 1 (one explicit instantiation per translation unit).
+template <int METHOD>
+cudaError_t launch_rk(const ImageDesc* descs, int n, long long total, int metric_mode, const SolverDesc& sol,
+                      const LaunchShape& shape, unsigned long long* queue, cudaStream_t stream);
+
 // metric_mode: 0 closed-form Kerr only, 1 tables only, 2 both (per-ray dispatch).
 cudaError_t launch_trace(const ImageDesc* descs, int n, long long total_rays, int metric_mode,
                          const SolverDesc& sol, const LaunchShape& shape,

@@ -64,6 +64,12 @@ cudaError_t launch_trace(const ImageDesc* descs, int n, long long total_rays, in
                          const SolverDesc& sol, const LaunchShape& shape, unsigned long long* queue,
                          cudaStream_t stream) {
     if (n < 1 || n > kMaxImagesPerLaunch) return cudaErrorInvalidValue;
+    if (sol.method != 0) {
+        if (sol.precision != 0 || metric_mode == 2) return cudaErrorInvalidValue;
+        if (sol.method == 1) return launch_rk<1>(descs, n, total_rays, metric_mode, sol, shape, queue, stream);
+        if (sol.method == 2) return launch_rk<2>(descs, n, total_rays, metric_mode, sol, shape, queue, stream);
+        return cudaErrorInvalidValue;
+    }
     if (sol.precision != 0) {
         if (metric_mode != 0) return cudaErrorInvalidValue;
         return launch_mixed(descs, n, total_rays, sol, shape, queue, stream);

@@ -49,14 +49,16 @@ __device__ __forceinline__ double step_factor(double err2) {
 }
 
 // ---------------------------------------------------------------------------
-// One Dormand-Prince step in FP64 (paper Sec. 3.2): returns the fifth-order
-// point yn, its flow kn (first-same-as-last) and H there, and the error vector.
+// One step of an embedded 5(4) pair in FP64 (paper Sec. 3.2): returns the
+// fifth-order point yn, the flow kn and H there, and the error vector.  For
+// Dormand-Prince kn is the seventh stage (first same as last); for Cash-Karp
+// and Fehlberg it is evaluated after the six stages.
 // ---------------------------------------------------------------------------
-template <int METRIC>
-__device__ __forceinline__ void dp5_step64(const ImageDesc& d, const KerrK& kk, const RayConst& R,
+template <int METRIC, int METHOD = 0>
+__device__ __forceinline__ void rk_step64(const ImageDesc& d, const KerrK& kk, const RayConst& R,
                                            const State& y, const State& k1, double h, State& yn,
                                            State& kn, double& Hn, State& err) {
-    using namespace dp;
+    using T = RK<METHOD>;
     State k2, k3, k4, k5, k6, ys;
     double Hs;
 #define TT_STAGE(dst, expr_r, expr_t, expr_p, expr_q)                                \
@@ -65,12 +67,12 @@ __device__ __forceinline__ void dp5_step64(const ImageDesc& d, const KerrK& kk, 
     ys.pr = fma(h, (expr_p), y.pr);                                                  \
     ys.pth = fma(h, (expr_q), y.pth);                                                \
     flow64<METRIC>(d, kk, R, ys, dst, Hs);
-#define TT_C2(f) (a21 * k1.f)
-#define TT_C3(f) fma(a32, k2.f, a31 * k1.f)
-#define TT_C4(f) fma(a43, k3.f, fma(a42, k2.f, a41 * k1.f))
-#define TT_C5(f) fma(a54, k4.f, fma(a53, k3.f, fma(a52, k2.f, a51 * k1.f)))
-#define TT_C6(f) fma(a65, k5.f, fma(a64, k4.f, fma(a63, k3.f, fma(a62, k2.f, a61 * k1.f))))
-#define TT_C7(f) fma(b6, k6.f, fma(b5, k5.f, fma(b4, k4.f, fma(b3, k3.f, b1 * k1.f))))
+#define TT_C2(f) (T::a21 * k1.f)
+#define TT_C3(f) fma(T::a32, k2.f, T::a31 * k1.f)
+#define TT_C4(f) fma(T::a43, k3.f, fma(T::a42, k2.f, T::a41 * k1.f))
+#define TT_C5(f) fma(T::a54, k4.f, fma(T::a53, k3.f, fma(T::a52, k2.f, T::a51 * k1.f)))
+#define TT_C6(f) fma(T::a65, k5.f, fma(T::a64, k4.f, fma(T::a63, k3.f, fma(T::a62, k2.f, T::a61 * k1.f))))
+#define TT_C7(f) fma(T::b6, k6.f, TT_MAC(T::b5, k5.f, fma(T::b4, k4.f, fma(T::b3, k3.f, T::b1 * k1.f))))
     TT_STAGE(k2, TT_C2(r), TT_C2(th), TT_C2(pr), TT_C2(pth))
     TT_STAGE(k3, TT_C3(r), TT_C3(th), TT_C3(pr), TT_C3(pth))
     TT_STAGE(k4, TT_C4(r), TT_C4(th), TT_C4(pr), TT_C4(pth))
@@ -81,7 +83,8 @@ __device__ __forceinline__ void dp5_step64(const ImageDesc& d, const KerrK& kk, 
     yn.pr = fma(h, TT_C7(pr), y.pr);
     yn.pth = fma(h, TT_C7(pth), y.pth);
     flow64<METRIC>(d, kk, R, yn, kn, Hn);
-#define TT_E(f) h * fma(e7, kn.f, fma(e6, k6.f, fma(e5, k5.f, fma(e4, k4.f, fma(e3, k3.f, e1 * k1.f)))))
+#define TT_E(f) \
+    h * TT_MAC(T::e7, kn.f, fma(T::e6, k6.f, fma(T::e5, k5.f, fma(T::e4, k4.f, fma(T::e3, k3.f, T::e1 * k1.f)))))
     err.r = TT_E(r);
     err.th = TT_E(th);
     err.pr = TT_E(pr);
@@ -116,7 +119,7 @@ __device__ __forceinline__ double err_norm2(const State& y, const State& yn, con
 // Crossing refinement.
 // Henon's exact step: integrate dz/dtheta = f / (dtheta/dlambda) for
 // z = (r, p_r, p_th) from the start of the accepted step to theta = pi/2 with
-// Dormand-Prince in 2^m equal sub-steps, m = 0..6, taking the first m whose
+// the ray's 5(4) pair in 2^m equal sub-steps, m = 0..6, taking the first m whose
 // largest sub-step error norm (over r, p_r, p_th) is <= 1.
 // ---------------------------------------------------------------------------
 template <int METRIC>
@@ -132,10 +135,10 @@ __device__ __forceinline__ void theta_flow64(const ImageDesc& d, const KerrK& kk
     g.pth = f.pth * it;
 }
 
-template <int METRIC>
+template <int METRIC, int METHOD = 0>
 __device__ double refine_henon64(const ImageDesc& d, const KerrK& kk, const RayConst& R,
                                  const State& y0, const State& f0, double atol, double rtol) {
-    using namespace dp;
+    using T = RK<METHOD>;
     const double dth_all = kHalfPi - y0.th;
     const double it0 = rcp64(f0.th);
     State g0;
@@ -157,24 +160,25 @@ __device__ double refine_henon64(const ImageDesc& d, const KerrK& kk, const RayC
     zs.pth = fma(dl, (eq), z.pth);                        \
     zs.th = fma(dl, (cc), th0);                           \
     theta_flow64<METRIC>(d, kk, R, zs, dst);
-#define TT_C2(f) (a21 * g.f)
-#define TT_C3(f) fma(a32, k2.f, a31 * g.f)
-#define TT_C4(f) fma(a43, k3.f, fma(a42, k2.f, a41 * g.f))
-#define TT_C5(f) fma(a54, k4.f, fma(a53, k3.f, fma(a52, k2.f, a51 * g.f)))
-#define TT_C6(f) fma(a65, k5.f, fma(a64, k4.f, fma(a63, k3.f, fma(a62, k2.f, a61 * g.f))))
-#define TT_C7(f) fma(b6, k6.f, fma(b5, k5.f, fma(b4, k4.f, fma(b3, k3.f, b1 * g.f))))
-            TT_HS(k2, c2, TT_C2(r), TT_C2(pr), TT_C2(pth))
-            TT_HS(k3, c3, TT_C3(r), TT_C3(pr), TT_C3(pth))
-            TT_HS(k4, c4, TT_C4(r), TT_C4(pr), TT_C4(pth))
-            TT_HS(k5, c5, TT_C5(r), TT_C5(pr), TT_C5(pth))
-            TT_HS(k6, 1.0, TT_C6(r), TT_C6(pr), TT_C6(pth))
+#define TT_C2(f) (T::a21 * g.f)
+#define TT_C3(f) fma(T::a32, k2.f, T::a31 * g.f)
+#define TT_C4(f) fma(T::a43, k3.f, fma(T::a42, k2.f, T::a41 * g.f))
+#define TT_C5(f) fma(T::a54, k4.f, fma(T::a53, k3.f, fma(T::a52, k2.f, T::a51 * g.f)))
+#define TT_C6(f) fma(T::a65, k5.f, fma(T::a64, k4.f, fma(T::a63, k3.f, fma(T::a62, k2.f, T::a61 * g.f))))
+#define TT_C7(f) fma(T::b6, k6.f, TT_MAC(T::b5, k5.f, fma(T::b4, k4.f, fma(T::b3, k3.f, T::b1 * g.f))))
+            TT_HS(k2, T::c2, TT_C2(r), TT_C2(pr), TT_C2(pth))
+            TT_HS(k3, T::c3, TT_C3(r), TT_C3(pr), TT_C3(pth))
+            TT_HS(k4, T::c4, TT_C4(r), TT_C4(pr), TT_C4(pth))
+            TT_HS(k5, T::c5, TT_C5(r), TT_C5(pr), TT_C5(pth))
+            TT_HS(k6, T::c6, TT_C6(r), TT_C6(pr), TT_C6(pth))
             State zn;
             zn.r = fma(dl, TT_C7(r), z.r);
             zn.pr = fma(dl, TT_C7(pr), z.pr);
             zn.pth = fma(dl, TT_C7(pth), z.pth);
             zn.th = th0 + dl;
             theta_flow64<METRIC>(d, kk, R, zn, k7);
-#define TT_E(f) dl * fma(e7, k7.f, fma(e6, k6.f, fma(e5, k5.f, fma(e4, k4.f, fma(e3, k3.f, e1 * g.f)))))
+#define TT_E(f) \
+    dl * TT_MAC(T::e7, k7.f, fma(T::e6, k6.f, fma(T::e5, k5.f, fma(T::e4, k4.f, fma(T::e3, k3.f, T::e1 * g.f)))))
             double s = sq_ratio(TT_E(r), z.r, zn.r, atol, rtol);
             s += sq_ratio(TT_E(pr), z.pr, zn.pr, atol, rtol);
             s += sq_ratio(TT_E(pth), z.pth, zn.pth, atol, rtol);
@@ -531,7 +535,7 @@ static __device__ double refine_henon32(const Lane& L, const State& y0, double r
 // Refine the pending crossing from the start of its step and record it.
 // PREC 0: FP64 Henon.  Mixed paths: Henon with FP32 stages, or in FP64 when
 // the solver asks for it (refine 2); emission is evaluated in FP64 either way.
-template <int METRIC, int PREC>
+template <int METRIC, int PREC, int METHOD = 0>
 __device__ void refine_pending(Lane& L, const SolverDesc& sol) {
     const ImageDesc& d = *L.d;
     double rc;
@@ -542,7 +546,7 @@ __device__ void refine_pending(Lane& L, const SolverDesc& sol) {
         double H0;
         flow64<METRIC>(d, L.kk, L.R, L.yc, f0, H0);
         L.hmax = fmax(L.hmax, fabs(H0));
-        rc = refine_henon64<METRIC>(d, L.kk, L.R, L.yc, f0, sol.atol, sol.rtol);
+        rc = refine_henon64<METRIC, METHOD>(d, L.kk, L.R, L.yc, f0, sol.atol, sol.rtol);
     }
     record_crossing<METRIC>(L, rc);
     L.pend = false;
@@ -550,15 +554,15 @@ __device__ void refine_pending(Lane& L, const SolverDesc& sol) {
 
 // A crossing was found in the step that starts at y (FP64).  Henon refinement
 // is deferred to a batched phase; crossings stay in order along the ray.
-template <int METRIC, int PREC>
+template <int METRIC, int PREC, int METHOD = 0>
 __device__ __forceinline__ void note_crossing(Lane& L, const State& y, const SolverDesc& sol) {
-    if (L.pend) refine_pending<METRIC, PREC>(L, sol);
+    if (L.pend) refine_pending<METRIC, PREC, METHOD>(L, sol);
     L.yc = y;
     L.pend = true;
 }
 
 // One FP64 step attempt; returns the termination code or -1 if the ray continues.
-template <int METRIC, int PREC>
+template <int METRIC, int PREC, int METHOD = 0>
 __device__ int step_ray64(Lane& L, const SolverDesc& sol) {
     const ImageDesc& d = *L.d;
     if ((long long)L.steps + (long long)L.rejects >= sol.max_steps) return 2;
@@ -566,7 +570,7 @@ __device__ int step_ray64(Lane& L, const SolverDesc& sol) {
     if (L.h < hmin) return 3;
     State yn, kn, e;
     double Hn;
-    dp5_step64<METRIC>(d, L.kk, L.R, L.y, L.k1, L.h, yn, kn, Hn, e);
+    rk_step64<METRIC, METHOD>(d, L.kk, L.R, L.y, L.k1, L.h, yn, kn, Hn, e);
     const double err2 = err_norm2(L.y, yn, e, sol.atol, sol.rtol);
     if (isnan(err2) || !isfinite(yn.r) || !isfinite(yn.th) || !isfinite(yn.pr) || !isfinite(yn.pth))
         return 4;
@@ -575,10 +579,10 @@ __device__ int step_ray64(Lane& L, const SolverDesc& sol) {
         if (d.disk && ((L.y.th <= kHalfPi) != (yn.th <= kHalfPi))) {
             if (sol.refine == 1) {
                 const double rc = refine_hermite64(L.y, L.k1, yn, kn, L.h);
-                if (L.pend) refine_pending<METRIC, PREC>(L, sol);
+                if (L.pend) refine_pending<METRIC, PREC, METHOD>(L, sol);
                 record_crossing<METRIC>(L, rc);
             } else {
-                note_crossing<METRIC, PREC>(L, L.y, sol);
+                note_crossing<METRIC, PREC, METHOD>(L, L.y, sol);
             }
         }
         L.lam += L.h;
@@ -759,11 +763,13 @@ __device__ __forceinline__ int find_image(const ImageDesc* descs, int n, long lo
 enum : int { kIdle = 0, kRun = 1, kDone = 2 };
 
 // PREC 0: FP64.  PREC 1: mixed with FP64 accumulation.  PREC 2: mixed with the
-// compensated FP32-pair accumulation.
-template <int METRIC, int PREC>
+// compensated FP32-pair accumulation.  METHOD (FP64 only): 0 Dormand-Prince,
+// 1 Cash-Karp, 2 Fehlberg.
+template <int METRIC, int PREC, int METHOD = 0>
 __device__ __forceinline__ void trace_loop(const ImageDesc* descs, int n_desc, long long total,
                                            const SolverDesc& sol, const TuneParams& tp,
                                            unsigned long long* queue) {
+    static_assert(PREC == 0 || METHOD == 0, "the mixed paths step with Dormand-Prince");
     constexpr int ACC = (PREC == 2) ? 1 : 0;
     const int lane = threadIdx.x & 31;
     Lane L;
@@ -778,7 +784,7 @@ __device__ __forceinline__ void trace_loop(const ImageDesc* descs, int n_desc, l
         const int n_free = __popc(__ballot_sync(kFull, st != kRun));
         if (n_free > 0 && (n_free >= tp.refill || n_free == 32) &&
             (!drained || __any_sync(kFull, st == kDone))) {
-            if (st != kIdle && L.pend) refine_pending<METRIC, PREC>(L, sol);
+            if (st != kIdle && L.pend) refine_pending<METRIC, PREC, METHOD>(L, sol);
             if (st == kDone) {
                 if (PREC != 0) check_h64<ACC>(L, yhi);
                 write_final(L, L.code);
@@ -812,7 +818,7 @@ __device__ __forceinline__ void trace_loop(const ImageDesc* descs, int n_desc, l
         // ---- step phases ---------------------------------------------------
         if (PREC == 0) {
             if (st == kRun) {
-                const int code = step_ray64<METRIC, 0>(L, sol);
+                const int code = step_ray64<METRIC, 0, METHOD>(L, sol);
                 if (code >= 0) {
                     L.code = code;
                     st = kDone;
@@ -859,7 +865,7 @@ __device__ __forceinline__ void trace_loop(const ImageDesc* descs, int n_desc, l
         // ---- batched crossing refinement -----------------------------------
         const unsigned pend = __ballot_sync(kFull, st == kRun && L.pend);
         if (pend && __popc(pend) >= tp.crossing_batch) {
-            if (st == kRun && L.pend) refine_pending<METRIC, PREC>(L, sol);
+            if (st == kRun && L.pend) refine_pending<METRIC, PREC, METHOD>(L, sol);
         }
         // ---- FP64 |H| monitor (mixed) --------------------------------------
         if (PREC != 0 && (iter % (unsigned)tp.monitor_period) == 0) {

@@ -191,7 +191,7 @@ def _camera(sc: Scene, pix_begin: int, pix_count: int) -> TTCamera:
 
 
 def solver_struct(sc: Scene) -> TTSolver:
-    return TTSolver(method=0, precision=sc.precision, rtol=sc.rtol, atol=sc.atol, h0=sc.h0, h_min=sc.h_min,
+    return TTSolver(method=sc.method, precision=sc.precision, rtol=sc.rtol, atol=sc.atol, h0=sc.h0, h_min=sc.h_min,
                     max_steps=sc.max_steps, horizon_eps=sc.horizon_eps, escape_factor=sc.escape_factor,
                     refine=sc.refine, fp64_radius_factor=sc.fp64_radius_factor,
                     fp64_pole_sin=sc.fp64_pole_sin)

@@ -131,7 +131,7 @@ def test_hamiltonian_flow(orc, r, th, M, a):
     sc = type("S", (), dict(metric_kind=0, M=M, a=a, table=None, r_min=0.0, r_max=0.0,
                             r_obs=1e3, theta_obs=1.0, nx=1, ny=1, alpha_min=0.0, alpha_max=1.0,
                             beta_min=0.0, beta_max=1.0, rtol=1e-10, atol=1e-10, h0=0.0, h_min=0.0,
-                            max_steps=10, horizon_eps=1e-3, escape_factor=1.1, refine=0,
+                            max_steps=10, horizon_eps=1e-3, escape_factor=1.1, refine=0, method=0,
                             disk_enabled=0, r_in=0.0, r_out=30.0, mdot=1.0, max_crossings=3, doppler=1))
     y = np.array([0.0, r, th, 0.0, *p])
     dy = orc.rhs(sc, y)
