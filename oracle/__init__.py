@@ -102,6 +102,8 @@ def lib():
             L.orc_rk_step.argtypes = [C.c_int, C.c_int, _FN, C.c_void_p, _D, _D, C.c_double, _D, _D, _D]
             L.orc_rk_tableau.argtypes = [C.c_int, _D, _D, _D, _D]
             L.orc_rk_tableau.restype = C.c_int
+            L.orc_gbs_step.argtypes = [C.c_int, _FN, C.c_void_p, _D, _D, C.c_double, C.c_int, _D, _D, _D]
+            L.orc_verlet_step.argtypes = [C.c_int, _FN, C.c_void_p, _D, C.c_double, _D, _D]
             i8 = C.POINTER(C.c_int8)
             i32 = C.POINTER(C.c_int32)
             L.orc_trace_ray.argtypes = [SP, C.c_double, C.c_double, C.c_int, _D, _D, _D,
@@ -266,22 +268,45 @@ def tableau(method: int = 0):
     return c[:st], a.reshape(7, 7)[:st, :st], b[:st], bh[:st]
 
 
-def dp5_step(f, y, h, method: int = 0):
-    """One step of the oracle's generic 5(4) stepper (default Dormand-Prince) on dy/dx = f(y)."""
-    y = np.ascontiguousarray(y, dtype=np.float64)
-    n = len(y)
-
+def _callback(f, n):
     def cb(_ctx, yp, dyp):
         yy = np.ctypeslib.as_array(yp, shape=(n,)).copy()
         d = np.asarray(f(yy), dtype=np.float64)
         for i in range(n):
             dyp[i] = d[i]
+    return _FN(cb)
 
-    fn = _FN(cb)
+
+def dp5_step(f, y, h, method: int = 0):
+    """One step of the oracle's generic 5(4) stepper (default Dormand-Prince) on dy/dx = f(y)."""
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    n = len(y)
+    fn = _callback(f, n)
     f0 = np.asarray(f(y.copy()), dtype=np.float64)
     yn, fnew, err = np.zeros(n), np.zeros(n), np.zeros(n)
     lib().orc_rk_step(method, n, fn, None, _dp(y), _dp(f0), h, _dp(yn), _dp(fnew), _dp(err))
     return yn, fnew, err
+
+
+def gbs_step(f, y, H, k):
+    """One Gragg-Bulirsch-Stoer macro-step with k extrapolation columns: (T_kk, f(T_kk), T_kk - T_k,k-1)."""
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    n = len(y)
+    fn = _callback(f, n)
+    f0 = np.asarray(f(y.copy()), dtype=np.float64)
+    yn, fnew, err = np.zeros(n), np.zeros(n), np.zeros(n)
+    lib().orc_gbs_step(n, fn, None, _dp(y), _dp(f0), H, k, _dp(yn), _dp(fnew), _dp(err))
+    return yn, fnew, err
+
+
+def verlet_step(f, y, h):
+    """One Stormer-Verlet step; y = (q, p), f(y) = (dH/dp, -dH/dq).  Returns (y_new, f(y_new))."""
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    n = len(y)
+    fn = _callback(f, n)
+    yn, fnew = np.zeros(n), np.zeros(n)
+    lib().orc_verlet_step(n, fn, None, _dp(y), h, _dp(yn), _dp(fnew))
+    return yn, fnew
 
 
 def kerr_table(M, a, nr, nth, r_min, r_max) -> np.ndarray:

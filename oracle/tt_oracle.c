@@ -445,6 +445,116 @@ void orc_dp5_step(int n, orc_fn f, void *ctx, const double *y, const double *f0,
     orc_rk_step(0, n, f, ctx, y, f0, h, ynew, fnew, err);
 }
 
+/* ------------------------------------------------------------------------ */
+/* Gragg-Bulirsch-Stoer (Sec. 3.2): over a macro-step H, Gragg's modified     */
+/* midpoint rule with n_j = 2j sub-steps (j = 1..k; no smoothing step), whose  */
+/* error has an expansion in even powers of H/n_j, then Aitken-Neville        */
+/* extrapolation of the k results to sub-step size 0 in (H/n_j)^2.            */
+/* Reading: k = 6 columns; the solution is the diagonal entry T_kk (order 2k) */
+/* and the error estimate T_kk - T_k,k-1; see the step control in trace_one.  */
+/* ------------------------------------------------------------------------ */
+
+#define ORC_GBS_KMAX 8
+#define ORC_GBS_K 6
+
+void orc_gbs_step(int n, orc_fn f, void *ctx, const double *y, const double *f0, double H, int k,
+                  double *ynew, double *fnew, double *err)
+{
+    double T[ORC_GBS_KMAX][ORC_GBS_KMAX][ORC_NMAX];   /* T[j-1][l-1] = T_{j,l} */
+    double z0[ORC_NMAX], z1[ORC_NMAX], z2[ORC_NMAX], fz[ORC_NMAX];
+    if (k < 1) k = 1;
+    if (k > ORC_GBS_KMAX) k = ORC_GBS_KMAX;
+    for (int j = 1; j <= k; ++j) {
+        int nj = 2 * j;
+        double h = H / (double)nj;
+        /* modified midpoint: z_1 = z_0 + h f(z_0), z_{m+1} = z_{m-1} + 2h f(z_m) */
+        for (int i = 0; i < n; ++i) {
+            z0[i] = y[i];
+            z1[i] = y[i] + h * f0[i];
+        }
+        for (int m = 1; m < nj; ++m) {
+            f(ctx, z1, fz);
+            for (int i = 0; i < n; ++i) {
+                z2[i] = z0[i] + 2.0 * h * fz[i];
+                z0[i] = z1[i];
+                z1[i] = z2[i];
+            }
+        }
+        for (int i = 0; i < n; ++i) T[j - 1][0][i] = z1[i];
+        /* Aitken-Neville in h^2: T_{j,l+1} = T_{j,l} + (T_{j,l} - T_{j-1,l}) / ((n_j / n_{j-l})^2 - 1) */
+        for (int l = 1; l < j; ++l) {
+            double ratio = (double)nj / (double)(2 * (j - l));
+            double den = ratio * ratio - 1.0;
+            for (int i = 0; i < n; ++i)
+                T[j - 1][l][i] = T[j - 1][l - 1][i] + (T[j - 1][l - 1][i] - T[j - 2][l - 1][i]) / den;
+        }
+    }
+    for (int i = 0; i < n; ++i) {
+        ynew[i] = T[k - 1][k - 1][i];
+        err[i] = (k > 1) ? T[k - 1][k - 1][i] - T[k - 1][k - 2][i] : 0.0;
+    }
+    f(ctx, ynew, fnew);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Verlet (Sec. 3.2): the Stormer-Verlet scheme for a general Hamiltonian     */
+/* H(q, p) (the generalised leapfrog; Hairer, Lubich & Wanner, Geometric      */
+/* Numerical Integration, Sec. VI.3), symmetric and symplectic, fixed step h: */
+/*   p+ = p - h/2 dH/dq(q, p+)                     (implicit in p+)           */
+/*   Q  = q + h/2 [dH/dp(q, p+) + dH/dp(Q, p+)]     (implicit in Q)           */
+/*   P  = p+ - h/2 dH/dq(Q, p+)                                                */
+/* The state holds q in its first n/2 and p in its last n/2 entries, and f    */
+/* returns (dH/dp, -dH/dq).  Reading: both implicit equations are solved by   */
+/* fixed-point iteration from the explicit guess, until no component moves    */
+/* by more than 1e-15 max(1, |value|), at most 50 iterations.                  */
+/* ------------------------------------------------------------------------ */
+
+#define ORC_VERLET_ITMAX 50
+
+static int moved(const double *a, const double *b, int m)
+{
+    for (int i = 0; i < m; ++i)
+        if (fabs(a[i] - b[i]) > 1e-15 * fmax(1.0, fabs(b[i]))) return 1;
+    return 0;
+}
+
+void orc_verlet_step(int n, orc_fn f, void *ctx, const double *y, double h, double *ynew, double *fnew)
+{
+    const int m = n / 2;
+    double w[ORC_NMAX], g[ORC_NMAX], nxt[ORC_NMAX], a[ORC_NMAX];
+    /* half kick: p+ = p + h/2 * (-dH/dq)(q, p+) */
+    memcpy(w, y, sizeof(double) * n);
+    f(ctx, w, g);
+    for (int i = 0; i < m; ++i) w[m + i] = y[m + i] + 0.5 * h * g[m + i];
+    for (int it = 0; it < ORC_VERLET_ITMAX; ++it) {
+        f(ctx, w, g);
+        for (int i = 0; i < m; ++i) nxt[i] = y[m + i] + 0.5 * h * g[m + i];
+        int mv = moved(nxt, w + m, m);
+        for (int i = 0; i < m; ++i) w[m + i] = nxt[i];
+        if (!mv) break;
+    }
+    /* drift: Q = q + h/2 (dH/dp(q, p+) + dH/dp(Q, p+)) */
+    f(ctx, w, g);                              /* w = (q, p+) */
+    for (int i = 0; i < m; ++i) {
+        a[i] = g[i];
+        w[i] = y[i] + h * a[i];
+    }
+    for (int it = 0; it < ORC_VERLET_ITMAX; ++it) {
+        f(ctx, w, g);
+        for (int i = 0; i < m; ++i) nxt[i] = y[i] + 0.5 * h * (a[i] + g[i]);
+        int mv = moved(nxt, w, m);
+        for (int i = 0; i < m; ++i) w[i] = nxt[i];
+        if (!mv) break;
+    }
+    /* second half kick, explicit */
+    f(ctx, w, g);                              /* w = (Q, p+) */
+    for (int i = 0; i < m; ++i) {
+        ynew[i] = w[i];
+        ynew[m + i] = w[m + i] + 0.5 * h * g[m + i];
+    }
+    f(ctx, ynew, fnew);
+}
+
 /* Reading (error norm): Hairer's mean-square norm over the dynamical
  * components r, theta, p_r, p_theta (t and phi are cyclic and never feed back;
  * p_t, p_phi are constants):
@@ -581,7 +691,8 @@ static void rhs_in_theta(void *ctx, const double *y, double *dy)
 
 /* Reading (refinement, default): Henon's exact-step method (M. Henon, Physica D
  * 5, 412, 1982).  From the start of the accepted step, integrate the system in
- * theta with the ray's 5(4) pair over Delta theta = pi/2 - theta_k, in 2^m equal
+ * theta with the ray's 5(4) pair (Dormand-Prince for the Gragg-Bulirsch-Stoer
+ * and Verlet rays) over Delta theta = pi/2 - theta_k, in 2^m equal
  * sub-steps, m = 0, 1, ... up to 6, taking the first m whose largest sub-step
  * error norm (over r, p_r, p_theta) is <= 1.  The main step sequence is not
  * changed. */
@@ -600,7 +711,7 @@ static double refine_henon(const orc_scene *s, const double *y0, const double *f
         }
         double worst = 0.0;
         for (int q = 0; q < nsub; ++q) {
-            orc_rk_step(s->method, 8, rhs_in_theta, &ctx, z, gz, dl, zn, gn, e);
+            orc_rk_step(s->method <= 2 ? s->method : 0, 8, rhs_in_theta, &ctx, z, gz, dl, zn, gn, e);
             double e2 = err_norm2(s, z, zn, e, idx3, 3);
             if (!(e2 <= worst)) worst = e2;     /* NaN-propagating max */
             memcpy(z, zn, sizeof z);
@@ -665,6 +776,24 @@ static int all_finite(const double *v, int n)
     return 1;
 }
 
+/* Reading (step control), the 5(4) pairs: h <- h min(facmax, max(0.2,
+ * 0.9 err^(-1/5))), facmax = 10, or 1 on the step right after a rejection.
+ * Gragg-Bulirsch-Stoer (with the controller constants of Hairer, Norsett &
+ * Wanner's extrapolation code): H <- H min(facmax, max(0.02,
+ * 0.94 (0.65 / err)^(1/(2k-1)))), facmax = 4, or 1 right after a rejection.
+ * Verlet: fixed step.  err = sqrt(err2); after a rejection err > 1, so both
+ * factors are below 1 there. */
+static double step_factor(int method, double err2, int after_reject)
+{
+    if (method == 4) return 1.0;
+    if (method == 3) {
+        double fac = (err2 == 0.0) ? 4.0 : 0.94 * pow(err2 / (0.65 * 0.65), -0.5 / (2.0 * ORC_GBS_K - 1.0));
+        return fmin(after_reject ? 1.0 : 4.0, fmax(0.02, fac));
+    }
+    double fac = (err2 == 0.0) ? 10.0 : 0.9 * pow(err2, -0.1);
+    return fmin(after_reject ? 1.0 : 10.0, fmax(0.2, fac));
+}
+
 static void trace_one(const orc_scene *s, const scene_consts *c, double alpha, double beta,
                       ray_result *res, int cap, double *lam_out, double *y_out, int *n_out)
 {
@@ -677,6 +806,8 @@ static void trace_one(const orc_scene *s, const scene_consts *c, double alpha, d
     }
     orc_rhs(s, y, f);
     res->h_max = fabs(orc_hamiltonian(s, y));
+    /* Verlet requires h0 > 0 (its fixed step); the adaptive methods start
+     * from h0 if given, else from the starting-step algorithm. */
     double h = (s->h0 > 0.0) ? s->h0 : initial_step(s, y, f);
     double lam = 0.0;
     int last_rejected = 0;
@@ -698,8 +829,17 @@ static void trace_one(const orc_scene *s, const scene_consts *c, double alpha, d
             res->code = ORC_UNDERFLOW;
             break;
         }
-        orc_rk_step(s->method, 8, rhs_cb, (void *)s, y, f, h, yn, fn, e);
-        double err2 = err_norm2(s, y, yn, e, NORM_IDX, 4);
+        double err2;
+        if (s->method == 4) {
+            orc_verlet_step(8, rhs_cb, (void *)s, y, h, yn, fn);
+            err2 = all_finite(yn, 8) ? 0.0 : NAN;          /* fixed step: always accepted */
+        } else {
+            if (s->method == 3)
+                orc_gbs_step(8, rhs_cb, (void *)s, y, f, h, ORC_GBS_K, yn, fn, e);
+            else
+                orc_rk_step(s->method, 8, rhs_cb, (void *)s, y, f, h, yn, fn, e);
+            err2 = err_norm2(s, y, yn, e, NORM_IDX, 4);
+        }
         if (isnan(err2) || !all_finite(yn, 8)) {
             res->code = ORC_NONFINITE;
             break;
@@ -750,17 +890,11 @@ static void trace_one(const orc_scene *s, const scene_consts *c, double alpha, d
                 res->code = ORC_ESCAPED;
                 break;
             }
-            /* Reading (step control): h <- h min(facmax, max(0.2, 0.9 err^(-1/5))),
-             * facmax = 10, or 1 on the step right after a rejection. */
-            double fac = (err2 == 0.0) ? 10.0 : 0.9 * pow(err2, -0.1);
-            double facmax = last_rejected ? 1.0 : 10.0;
-            fac = fmin(facmax, fmax(0.2, fac));
-            h *= fac;
+            h *= step_factor(s->method, err2, last_rejected);
             last_rejected = 0;
         } else {
             res->rejects++;
-            double fac = fmax(0.2, 0.9 * pow(err2, -0.1));
-            h *= fac;
+            h *= step_factor(s->method, err2, 1);
             last_rejected = 1;
         }
     }

@@ -57,7 +57,8 @@ typedef struct {
     double horizon_eps;      /* captured when r < r_h (1 + eps) */
     double escape_factor;    /* escaped when r > factor * r_obs */
     int    refine;           /* 0 = Henon exact-step, 1 = cubic-Hermite + bisection */
-    int    method;           /* 0 = Dormand-Prince, 1 = Cash-Karp, 2 = Fehlberg (5(4) pairs) */
+    int    method;           /* 0 = Dormand-Prince, 1 = Cash-Karp, 2 = Fehlberg (5(4) pairs),
+                                3 = Gragg-Bulirsch-Stoer, 4 = Verlet (fixed step h0 > 0) */
     /* disk (Sec. 2.3-2.4) */
     int    disk_enabled;
     double r_in;             /* <= 0: prograde ISCO of (M, a) */
@@ -104,6 +105,9 @@ void orc_rk_step(int method, int n, orc_fn f, void *ctx, const double *y, const 
 int  orc_rk_tableau(int method, double c[7], double a[49], double b[7], double bhat[7]);
 void orc_dp5_step(int n, orc_fn f, void *ctx, const double *y, const double *f0,
                   double h, double *ynew, double *fnew, double *err);
+void orc_gbs_step(int n, orc_fn f, void *ctx, const double *y, const double *f0, double H, int k,
+                  double *ynew, double *fnew, double *err);
+void orc_verlet_step(int n, orc_fn f, void *ctx, const double *y, double h, double *ynew, double *fnew);
 void orc_dp5_tableau(double c[7], double a[49], double b[7], double bhat[7]);
 
 /* ---- one ray with its accepted-step trajectory (for the pins) ----

@@ -28,7 +28,7 @@ import numpy as np
 
 FP64, MIXED, MIXED_PAIR = 0, 1, 2
 REFINE_HENON, REFINE_HERMITE, REFINE_HENON64 = 0, 1, 2
-DOPRI5, CASH_KARP, FEHLBERG = 0, 1, 2
+DOPRI5, CASH_KARP, FEHLBERG, GBS, VERLET = 0, 1, 2, 3, 4
 METRIC_KERR, METRIC_TABLE = 0, 1
 
 
@@ -61,7 +61,7 @@ class Scene:
     horizon_eps: float = 1e-3
     escape_factor: float = 1.1
     refine: int = REFINE_HENON
-    method: int = DOPRI5              # embedded 5(4) pair
+    method: int = DOPRI5              # integrator (Verlet: fixed step h0 > 0)
     fp64_radius_factor: float = 0.0   # mixed paths: FP64 steps below factor * r_h (0: 1.5, < 0: none)
     fp64_pole_sin: float = 0.0        # mixed paths: FP64 steps where sin(theta) < this (0: 0.1, < 0: none)
     # disk
