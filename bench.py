@@ -38,8 +38,18 @@ FLOPS_PER_STEP = 6 * 65 + 232 + 20 + 5
 # Cash-Karp and Fehlberg also evaluate the flow six times per step attempt (five
 # stages and the new point); their stage sums have one (Fehlberg: e_7 = 0) or two
 # (Cash-Karp: b_5 = e_7 = 0) fewer FMA per state component.
-FLOPS_PER_STEP_METHOD = {0: FLOPS_PER_STEP, 1: FLOPS_PER_STEP - 2 * 2 * 4, 2: FLOPS_PER_STEP - 2 * 4}
-METHODS = {"dopri5": 0, "cash_karp": 1, "fehlberg": 2}
+# Gragg-Bulirsch-Stoer macro-step (6 columns, 2..12 sub-steps): 36 chain flows + the flow at
+# the new point, 12 flops per chain sub-step (y + d, d0 + 2h f), 6 x (4 + 1) to start the
+# chains, 15 Aitken-Neville updates x 4 components x 3, the new point and the error (8),
+# norm 20, control 5.
+FLOPS_PER_GBS_STEP = 37 * 65 + 36 * 12 + 6 * 5 + 15 * 4 * 3 + 8 + 20 + 5
+FLOPS_PER_STEP_METHOD = {0: FLOPS_PER_STEP, 1: FLOPS_PER_STEP - 2 * 2 * 4, 2: FLOPS_PER_STEP - 2 * 4,
+                         3: FLOPS_PER_GBS_STEP}
+METHODS = {"dopri5": 0, "cash_karp": 1, "fehlberg": 2, "gbs": 3, "verlet": 4}
+# Verlet's fixed step (the paper gives none) and its capture radius: the paper's own
+# stop of its Fig. 2 test (2.05 M at a = 0, eps = 0.025); closer in, p_r ~ 1/Delta
+# outruns any fixed step and the implicit half steps diverge
+VERLET_H, VERLET_EPS, VERLET_N = 0.01, 0.025, 128
 METHOD_NAMES = {v: k for k, v in METHODS.items()}
 # The same count for an FP32 step of the mixed paths (the rearranged FP32 flow is 72).
 FLOPS_PER_STEP_F32 = 6 * 72 + 232 + 20 + 5
@@ -65,9 +75,9 @@ def parse():
                    help="path of the main measurement (default: the FP64 headline)")
     p.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision objects")
     p.add_argument("--method", default="dopri5", choices=list(METHODS),
-                   help="5(4) pair of the FP64 run (default: Dormand-Prince, the headline)")
+                   help="integrator of the FP64 run (default: Dormand-Prince, the headline)")
     p.add_argument("--no-pairs", action="store_true",
-                   help="skip the Cash-Karp / Fehlberg objects of the default line")
+                   help="skip the objects of the other four integrators in the default line")
     p.add_argument("--workload", default="kerr_disk", choices=["kerr_disk", "batch", "table"],
                    help="kerr_disk: the 1024^2 headline image (default); batch: 64 uneven images in one "
                         "persistent launch, replayed from a CUDA graph; table: the 4096^2 tabulated-metric image")
@@ -87,7 +97,10 @@ PRECISIONS = {"fp64": 0, "mixed": 1, "mixed_pair": 2}
 def workload(n, precision="fp64", method="dopri5"):
     from paper_2609_08989_gb300 import scenes
     if precision == "fp64":
-        return scenes.kerr_disk(n).replace(method=METHODS[method])
+        sc = scenes.kerr_disk(n).replace(method=METHODS[method])
+        if method == "verlet":
+            sc = sc.replace(h0=VERLET_H, horizon_eps=VERLET_EPS, name=sc.name + "_verlet")
+        return sc
     if method != "dopri5":
         raise SystemExit("the mixed-precision paths step with Dormand-Prince only")
     return scenes.kerr_disk_mixed(n).replace(precision=PRECISIONS[precision])
@@ -316,21 +329,30 @@ def run_tartarus(args):
                            "rk_step_attempts_per_image": int(mout["steps"].sum().item() + mout["rejects"].sum().item())}
     pairs = {}
     if not args.no_pairs and args.precision == "fp64" and args.method == "dopri5":
-        # the other two 5(4) pairs of Sec. 3.2 on the same image, same tolerance
-        for name in ("cash_karp", "fehlberg"):
-            psc = workload(args.n, "fp64", name)
+        # the other four integrators of Sec. 3.2 on the same scene and tolerance
+        # (Verlet: fixed step VERLET_H on a VERLET_N^2 camera, which it needs ~10^5 steps per ray for)
+        for name in ("cash_karp", "fehlberg", "gbs", "verlet"):
+            psc = workload(VERLET_N if name == "verlet" else args.n, "fp64", name)
             ms, pout = time_variant(T, psc, max(2, args.steps // 2), 1, flush)
             h = pout["h_max"].cpu().numpy()
-            esc = pout["code"].cpu().numpy() == 0
+            code = pout["code"].cpu().numpy()
+            esc = code == 0
             att = int(pout["steps"].sum().item() + pout["rejects"].sum().item())
-            pach = FLOPS_PER_STEP_METHOD[psc.method] * att / (ms / 1e3) / 1e12
             pairs[name] = {"value": psc.npix / (ms / 1e3), "unit": UNIT, "ms_per_image": ms,
-                           "rk_step_attempts_per_image": att,
+                           "workload": psc.name, "step_attempts_per_image": att,
+                           "steps_per_ray": att / psc.npix,
+                           "h_max_escaped_median": float(np.median(h[esc])) if esc.any() else None,
                            "h_max_escaped": float(h[esc].max()) if esc.any() else None,
-                           "fp64_tflops": pach, "frac": pach / FP64_PEAK_TFLOPS}
+                           "captured": int((code == 1).sum()), "other_codes": int((code > 1).sum())}
+            if psc.method in FLOPS_PER_STEP_METHOD:
+                pach = FLOPS_PER_STEP_METHOD[psc.method] * att / (ms / 1e3) / 1e12
+                pairs[name].update({"fp64_tflops": pach, "frac": pach / FP64_PEAK_TFLOPS})
+            else:
+                pairs[name].update({"h0": psc.h0, "horizon_eps": psc.horizon_eps,
+                                    "note": "flops per step vary with the fixed-point iterations: no roofline"})
     if rank == 0:
-        flops = FLOPS_PER_STEP_METHOD[sc.method] * step_attempts
-        achieved = flops / (mean_kern / 1e3) / 1e12
+        fpu = FLOPS_PER_STEP_METHOD.get(sc.method, 0)
+        achieved = fpu * step_attempts / (mean_kern / 1e3) / 1e12
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -346,7 +368,7 @@ def run_tartarus(args):
                          "kernel": ("trace_kernel64_b256<0,1>" if sc.method == 0
                                     else "trace_kernel_rk<%d,0,1,256>" % sc.method), "kernel_ms": mean_kern,
                          "peak_source": "FP64 pipe: 152 SMs x 2070 MHz x 2 DFMA/clk (derived)",
-                         "flops_per_unit": FLOPS_PER_STEP_METHOD[sc.method],
+                         "flops_per_unit": fpu,
                          "unit_of_work": "%s step attempt" % METHOD_NAMES[sc.method]},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": DESC_BYTES,
                     "d2h_bytes_per_step": BYTES_OUT_PER_PIXEL * sc.npix},
@@ -356,9 +378,11 @@ def run_tartarus(args):
         if args.precision != "fp64":
             line["dtype"] = "f32 stages / f64 state" if args.precision == "mixed" else "f32 stages / f32-pair state"
             line["roofline"] = None          # the FP64 flop count does not describe the mixed step
+        if sc.method not in FLOPS_PER_STEP_METHOD:
+            line["roofline"] = None          # Verlet: flops per step vary with its fixed-point iterations
         line.update(mixed)
         if pairs:
-            line["pairs"] = pairs
+            line["integrators"] = pairs
         if not args.no_cpu_baseline:
             v, rays, cores, tsec = time_oracle(sc, args.cpu_seconds)
             line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",

@@ -64,6 +64,8 @@ extern "C" {
 #define TT_DP54          0   /* Dormand-Prince 5(4) (paper Sec. 3.2)   */
 #define TT_CK45          1   /* Cash-Karp 5(4) (paper Sec. 3.2), FP64 only */
 #define TT_F45           2   /* Fehlberg 5(4) (paper Sec. 3.2), FP64 only  */
+#define TT_GBS           3   /* Gragg-Bulirsch-Stoer extrapolation (Sec. 3.2), FP64 only */
+#define TT_VERLET        4   /* Stormer-Verlet, fixed step h0 > 0 (Sec. 3.2), FP64 only  */
 #define TT_FP64          0   /* all arithmetic in binary64             */
 #define TT_MIXED         1   /* FP32 stages, FP64 state accumulation   */
 #define TT_MIXED_PAIR    2   /* FP32 stages, compensated FP32-pair state accumulation (~48 bits) */
@@ -108,15 +110,25 @@ typedef struct {
  * largest |H| evaluated in FP64: at the start, at every FP64 step, at the
  * start of every step with a disk crossing, every monitor_period warp
  * iterations and at the end.
- * method: the embedded 5(4) pair of Sec. 3.2; each propagates its fifth-order
- * solution and takes the difference to its fourth-order one as the error
- * estimate.  TT_CK45 and TT_F45 run in FP64 only (other precisions return
- * TT_EUNSUPPORTED), for either metric kind, but a batch that mixes closed-form
- * Kerr and tabulated images returns TT_EUNSUPPORTED for them, with nothing
- * launched; other methods give TT_EINVAL.  tt_tune.reg_variant applies to
+ * method: one of the five integrators of Sec. 3.2.  The embedded 5(4) pairs
+ * (TT_DP54, TT_CK45, TT_F45) propagate their fifth-order solution and take the
+ * difference to the fourth-order one as the error estimate.  TT_GBS: macro-
+ * steps of Gragg's modified midpoint rule with 2, 4, ..., 12 sub-steps,
+ * extrapolated in h^2 (Aitken-Neville, 6 columns); the error estimate is the
+ * difference of the two highest-order entries, and the step adapts with the
+ * factor 0.94 (0.65/err)^(1/11), clamped to [0.02, 4].  TT_VERLET: the
+ * Stormer-Verlet scheme for the non-separable H (implicit half steps solved by
+ * fixed-point iteration to 1e-15 relative, at most 50 iterations) with the
+ * fixed step h0, which must be > 0 (TT_EINVAL otherwise); rtol/atol are unused
+ * and rejects stay 0.  Every method other than TT_DP54 runs in FP64 only
+ * (other precisions return TT_EUNSUPPORTED), for either metric kind, but a
+ * batch that mixes closed-form Kerr and tabulated images returns
+ * TT_EUNSUPPORTED for them, with nothing launched; other values of method give
+ * TT_EINVAL.  With TT_REFINE_HENON, crossings of TT_GBS and TT_VERLET rays are
+ * refined with Dormand-Prince sub-steps.  tt_tune.reg_variant applies to
  * TT_DP54 only. */
 typedef struct {
-    int method;                 /* TT_DP54, TT_CK45 or TT_F45 */
+    int method;                 /* TT_DP54, TT_CK45, TT_F45, TT_GBS or TT_VERLET */
     int precision;              /* TT_FP64, TT_MIXED or TT_MIXED_PAIR */
     double rtol, atol, h0, h_min;
     long long max_steps;

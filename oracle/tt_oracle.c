@@ -452,6 +452,10 @@ void orc_dp5_step(int n, orc_fn f, void *ctx, const double *y, const double *f0,
 /* extrapolation of the k results to sub-step size 0 in (H/n_j)^2.            */
 /* Reading: k = 6 columns; the solution is the diagonal entry T_kk (order 2k) */
 /* and the error estimate T_kk - T_k,k-1; see the step control in trace_one.  */
+/* The midpoint chain and the extrapolation act on the increment z - y0, the  */
+/* same values in exact arithmetic: the error estimate is a small difference  */
+/* of the extrapolated values, and increments keep the rounding in it         */
+/* relative to the step's change instead of to |y| (r ~ 10^3 here).           */
 /* ------------------------------------------------------------------------ */
 
 #define ORC_GBS_KMAX 8
@@ -460,27 +464,29 @@ void orc_dp5_step(int n, orc_fn f, void *ctx, const double *y, const double *f0,
 void orc_gbs_step(int n, orc_fn f, void *ctx, const double *y, const double *f0, double H, int k,
                   double *ynew, double *fnew, double *err)
 {
-    double T[ORC_GBS_KMAX][ORC_GBS_KMAX][ORC_NMAX];   /* T[j-1][l-1] = T_{j,l} */
-    double z0[ORC_NMAX], z1[ORC_NMAX], z2[ORC_NMAX], fz[ORC_NMAX];
+    double T[ORC_GBS_KMAX][ORC_GBS_KMAX][ORC_NMAX];   /* T[j-1][l-1] = T_{j,l} - y */
+    double d0[ORC_NMAX], d1[ORC_NMAX], d2[ORC_NMAX], z[ORC_NMAX], fz[ORC_NMAX];
     if (k < 1) k = 1;
     if (k > ORC_GBS_KMAX) k = ORC_GBS_KMAX;
     for (int j = 1; j <= k; ++j) {
         int nj = 2 * j;
         double h = H / (double)nj;
-        /* modified midpoint: z_1 = z_0 + h f(z_0), z_{m+1} = z_{m-1} + 2h f(z_m) */
+        /* modified midpoint on the increment d = z - y: d_0 = 0, d_1 = h f(y),
+         * d_{m+1} = d_{m-1} + 2h f(y + d_m) */
         for (int i = 0; i < n; ++i) {
-            z0[i] = y[i];
-            z1[i] = y[i] + h * f0[i];
+            d0[i] = 0.0;
+            d1[i] = h * f0[i];
         }
         for (int m = 1; m < nj; ++m) {
-            f(ctx, z1, fz);
+            for (int i = 0; i < n; ++i) z[i] = y[i] + d1[i];
+            f(ctx, z, fz);
             for (int i = 0; i < n; ++i) {
-                z2[i] = z0[i] + 2.0 * h * fz[i];
-                z0[i] = z1[i];
-                z1[i] = z2[i];
+                d2[i] = d0[i] + 2.0 * h * fz[i];
+                d0[i] = d1[i];
+                d1[i] = d2[i];
             }
         }
-        for (int i = 0; i < n; ++i) T[j - 1][0][i] = z1[i];
+        for (int i = 0; i < n; ++i) T[j - 1][0][i] = d1[i];
         /* Aitken-Neville in h^2: T_{j,l+1} = T_{j,l} + (T_{j,l} - T_{j-1,l}) / ((n_j / n_{j-l})^2 - 1) */
         for (int l = 1; l < j; ++l) {
             double ratio = (double)nj / (double)(2 * (j - l));
@@ -490,7 +496,7 @@ void orc_gbs_step(int n, orc_fn f, void *ctx, const double *y, const double *f0,
         }
     }
     for (int i = 0; i < n; ++i) {
-        ynew[i] = T[k - 1][k - 1][i];
+        ynew[i] = y[i] + T[k - 1][k - 1][i];
         err[i] = (k > 1) ? T[k - 1][k - 1][i] - T[k - 1][k - 2][i] : 0.0;
     }
     f(ctx, ynew, fnew);
@@ -691,8 +697,9 @@ static void rhs_in_theta(void *ctx, const double *y, double *dy)
 
 /* Reading (refinement, default): Henon's exact-step method (M. Henon, Physica D
  * 5, 412, 1982).  From the start of the accepted step, integrate the system in
- * theta with the ray's 5(4) pair (Dormand-Prince for the Gragg-Bulirsch-Stoer
- * and Verlet rays) over Delta theta = pi/2 - theta_k, in 2^m equal
+ * theta with the ray's own adaptive integrator (a 5(4) pair, or the
+ * extrapolator; Dormand-Prince for Verlet rays) over Delta theta = pi/2 -
+ * theta_k, in 2^m equal
  * sub-steps, m = 0, 1, ... up to 6, taking the first m whose largest sub-step
  * error norm (over r, p_r, p_theta) is <= 1.  The main step sequence is not
  * changed. */
@@ -711,7 +718,10 @@ static double refine_henon(const orc_scene *s, const double *y0, const double *f
         }
         double worst = 0.0;
         for (int q = 0; q < nsub; ++q) {
-            orc_rk_step(s->method <= 2 ? s->method : 0, 8, rhs_in_theta, &ctx, z, gz, dl, zn, gn, e);
+            if (s->method == 3)
+                orc_gbs_step(8, rhs_in_theta, &ctx, z, gz, dl, ORC_GBS_K, zn, gn, e);
+            else
+                orc_rk_step(s->method <= 2 ? s->method : 0, 8, rhs_in_theta, &ctx, z, gz, dl, zn, gn, e);
             double e2 = err_norm2(s, z, zn, e, idx3, 3);
             if (!(e2 <= worst)) worst = e2;     /* NaN-propagating max */
             memcpy(z, zn, sizeof z);

@@ -56,11 +56,12 @@ int check_metric(const tt_metric* m) {
 
 int check_solver(const tt_solver* s) {
     if (!s) return TT_EINVAL;
-    if (s->method != TT_DP54 && s->method != TT_CK45 && s->method != TT_F45) return TT_EINVAL;
+    if (s->method < TT_DP54 || s->method > TT_VERLET) return TT_EINVAL;
     if (s->precision != TT_FP64 && s->precision != TT_MIXED && s->precision != TT_MIXED_PAIR) return TT_EINVAL;
     if (s->method != TT_DP54 && s->precision != TT_FP64) return TT_EUNSUPPORTED;
     if (!is_finite(s->rtol) || !is_finite(s->atol) || !(s->rtol > 0.0) || !(s->atol > 0.0)) return TT_EINVAL;
     if (!is_finite(s->h0) || !is_finite(s->h_min)) return TT_EINVAL;
+    if (s->method == TT_VERLET && !(s->h0 > 0.0)) return TT_EINVAL;     // Verlet's fixed step
     if (s->max_steps < 1) return TT_EINVAL;
     if (!is_finite(s->horizon_eps) || s->horizon_eps < 0.0) return TT_EINVAL;
     if (!is_finite(s->escape_factor) || !(s->escape_factor > 1.0)) return TT_EINVAL;
@@ -238,8 +239,9 @@ int check_shape(const tt_tune* t) {
     return TT_OK;
 }
 
-// The Cash-Karp and Fehlberg kernels take one metric kind per launch: a batch
-// with both closed-form Kerr and tabulated images is refused for them.
+// The kernels of the integrators other than Dormand-Prince take one metric
+// kind per launch: a batch with both closed-form Kerr and tabulated images is
+// refused for them.
 int check_kinds(const tt_image* images, int n, const tt_solver* s) {
     if (s->method == TT_DP54) return TT_OK;
     bool kerr = false, table = false;

@@ -64,7 +64,7 @@ struct SolverDesc {
     long long max_steps;
     int refine;                   // 0 Henon, 1 Hermite, 2 Henon in FP64 on the mixed paths too
     int precision;                // 0 FP64, 1 mixed (FP64 state), 2 mixed (FP32-pair state)
-    int method;                   // 0 Dormand-Prince, 1 Cash-Karp, 2 Fehlberg (FP64 only)
+    int method;                   // 0 Dormand-Prince; FP64 only: 1 Cash-Karp, 2 Fehlberg, 3 GBS, 4 Verlet
 };
 
 struct LaunchShape {
@@ -102,8 +102,9 @@ struct LaunchParams {
 };
 
 // Enqueue the persistent tracing kernel over n <= kMaxImagesPerLaunch images.
-// FP64 kernels of the Cash-Karp (METHOD 1) and Fehlberg (METHOD 2) pairs for
-// metric_mode 0 or 1 (one explicit instantiation per translation unit).
+// FP64 kernels of the Cash-Karp (METHOD 1) and Fehlberg (2) pairs, the
+// Gragg-Bulirsch-Stoer extrapolator (3) and Verlet (4) for metric_mode 0 or 1
+// (one explicit instantiation per translation unit).
 template <int METHOD>
 cudaError_t launch_rk(const ImageDesc* descs, int n, long long total, int metric_mode, const SolverDesc& sol,
                       const LaunchShape& shape, unsigned long long* queue, cudaStream_t stream);

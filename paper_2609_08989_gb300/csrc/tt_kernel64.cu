@@ -68,6 +68,8 @@ cudaError_t launch_trace(const ImageDesc* descs, int n, long long total_rays, in
         if (sol.precision != 0 || metric_mode == 2) return cudaErrorInvalidValue;
         if (sol.method == 1) return launch_rk<1>(descs, n, total_rays, metric_mode, sol, shape, queue, stream);
         if (sol.method == 2) return launch_rk<2>(descs, n, total_rays, metric_mode, sol, shape, queue, stream);
+        if (sol.method == 3) return launch_rk<3>(descs, n, total_rays, metric_mode, sol, shape, queue, stream);
+        if (sol.method == 4) return launch_rk<4>(descs, n, total_rays, metric_mode, sol, shape, queue, stream);
         return cudaErrorInvalidValue;
     }
     if (sol.precision != 0) {

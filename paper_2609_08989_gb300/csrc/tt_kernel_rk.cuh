@@ -1,7 +1,9 @@
-// tt_kernel_rk.cuh -- FP64 persistent tracing kernels for the Cash-Karp and
-// Fehlberg 5(4) pairs (paper Sec. 3.2), closed-form Kerr (128 or 256 threads)
-// and tabulated metrics (128 threads).  Each pair is built in a translation
-// unit of its own, which defines TT_RK_METHOD and includes this file.
+// tt_kernel_rk.cuh -- FP64 persistent tracing kernels for the integrators of
+// paper Sec. 3.2 other than Dormand-Prince: the Cash-Karp (1) and Fehlberg (2)
+// 5(4) pairs, the Gragg-Bulirsch-Stoer extrapolator (3) and Verlet (4), for
+// closed-form Kerr (128 or 256 threads) and tabulated metrics (128 threads).
+// Each integrator is built in a translation unit of its own, which defines
+// TT_RK_METHOD and includes this file.
 #pragma once
 
 #include "tt_trace.cuh"

@@ -99,6 +99,133 @@ __device__ __forceinline__ void rk_step64(const ImageDesc& d, const KerrK& kk, c
 #undef TT_C7
 }
 
+// ---------------------------------------------------------------------------
+// Gragg-Bulirsch-Stoer macro-step in FP64 (paper Sec. 3.2): Gragg's modified
+// midpoint rule with n_j = 2j sub-steps (j = 1..kGbsK, no smoothing step), each
+// result extrapolated to sub-step 0 in (H/n_j)^2 by Aitken-Neville; the
+// solution is the diagonal entry T_kk and the error T_kk - T_k,k-1.  Chain and
+// extrapolation run on the increment z - y (so the rounding in the error
+// estimate, a small difference of extrapolated values, scales with the step's
+// change rather than with |y|).  The table row lives in registers (the j and l
+// loops unroll, so each weight 1 / ((j / (j - l))^2 - 1) is a constant).
+// ---------------------------------------------------------------------------
+constexpr int kGbsK = 6;
+
+__device__ __forceinline__ State axpy(double a, const State& x, const State& y) {
+    return State{fma(a, x.r, y.r), fma(a, x.th, y.th), fma(a, x.pr, y.pr), fma(a, x.pth, y.pth)};
+}
+
+__device__ __forceinline__ State sub(const State& x, const State& y) {
+    return State{x.r - y.r, x.th - y.th, x.pr - y.pr, x.pth - y.pth};
+}
+
+__device__ __forceinline__ State add(const State& x, const State& y) {
+    return State{x.r + y.r, x.th + y.th, x.pr + y.pr, x.pth + y.pth};
+}
+
+// dT = T_kk - y, err = T_kk - T_k,k-1 for dz/dx = flow(z) from (y, f0 = flow(y)) over H.
+template <class Flow>
+__device__ __forceinline__ void gbs_core(const State& y, const State& f0, double H, Flow&& flow, State& dT,
+                                         State& err) {
+    State T[kGbsK];
+#pragma unroll
+    for (int j = 1; j <= kGbsK; ++j) {
+        const double h = H / (double)(2 * j);
+        State d0 = State{0.0, 0.0, 0.0, 0.0};
+        State d1 = State{h * f0.r, h * f0.th, h * f0.pr, h * f0.pth};
+        for (int m = 1; m < 2 * j; ++m) {
+            State fz;
+            flow(add(y, d1), fz);
+            const State d2 = axpy(2.0 * h, fz, d0);
+            d0 = d1;
+            d1 = d2;
+        }
+        if (j == 1) {
+            T[0] = d1;
+        } else {
+            State prev = T[0];                  // T_{j-1,1}
+            T[0] = d1;
+#pragma unroll
+            for (int l = 1; l < j; ++l) {
+                const double ratio = (double)j / (double)(j - l);
+                const double w = 1.0 / (ratio * ratio - 1.0);
+                const State old = T[l];         // T_{j-1,l+1}
+                T[l] = axpy(w, sub(T[l - 1], prev), T[l - 1]);
+                prev = old;
+            }
+        }
+    }
+    dT = T[kGbsK - 1];
+    err = sub(T[kGbsK - 1], T[kGbsK - 2]);
+}
+
+template <int METRIC>
+__device__ __forceinline__ void gbs_step64(const ImageDesc& d, const KerrK& kk, const RayConst& R,
+                                           const State& y, const State& f0, double H, State& yn, State& kn,
+                                           double& Hn, State& err) {
+    State dT;
+    gbs_core(y, f0, H, [&](const State& z, State& fz) {
+        double Hs;
+        flow64<METRIC>(d, kk, R, z, fz, Hs);
+    }, dT, err);
+    yn = add(y, dT);
+    flow64<METRIC>(d, kk, R, yn, kn, Hn);
+}
+
+// Step factor of the extrapolator: 0.94 (0.65 / err)^(1/(2k-1)) from err^2.
+__device__ __forceinline__ double gbs_factor(double err2) {
+    return (err2 == 0.0) ? 4.0 : 0.94 * pow(err2 / (0.65 * 0.65), -0.5 / (2.0 * kGbsK - 1.0));
+}
+
+// ---------------------------------------------------------------------------
+// Stormer-Verlet for the Hamiltonian H(q, p), q = (r, theta), p = (p_r, p_theta)
+// (paper Sec. 3.2; the generalised leapfrog of Hairer, Lubich & Wanner):
+//   p+ = p - h/2 dH/dq(q, p+),  Q = q + h/2 [dH/dp(q, p+) + dH/dp(Q, p+)],
+//   P = p+ - h/2 dH/dq(Q, p+),
+// both implicit equations solved by fixed-point iteration from the explicit
+// guess until no component moves by more than 1e-15 max(1, |value|), at most
+// kVerletIt iterations.  The flow gives (dH/dp, -dH/dq) = (r', theta', p_r', p_theta').
+// ---------------------------------------------------------------------------
+constexpr int kVerletIt = 50;
+
+__device__ __forceinline__ bool moved2(double a0, double b0, double a1, double b1) {
+    return fabs(a0 - b0) > 1e-15 * fmax(1.0, fabs(b0)) || fabs(a1 - b1) > 1e-15 * fmax(1.0, fabs(b1));
+}
+
+template <int METRIC>
+__device__ __forceinline__ void verlet_step64(const ImageDesc& d, const KerrK& kk, const RayConst& R,
+                                              const State& y, const State& f0, double h, State& yn, State& kn,
+                                              double& Hn) {
+    const double hh = 0.5 * h;
+    State w = y, g;
+    double Hs;
+    w.pr = fma(hh, f0.pr, y.pr);
+    w.pth = fma(hh, f0.pth, y.pth);
+    for (int it = 0; it < kVerletIt; ++it) {
+        flow64<METRIC>(d, kk, R, w, g, Hs);
+        const double npr = fma(hh, g.pr, y.pr), npth = fma(hh, g.pth, y.pth);
+        const bool mv = moved2(npr, w.pr, npth, w.pth);
+        w.pr = npr;
+        w.pth = npth;
+        if (!mv) break;
+    }
+    flow64<METRIC>(d, kk, R, w, g, Hs);         // w = (q, p+)
+    const double ar = g.r, ath = g.th;
+    w.r = fma(h, ar, y.r);
+    w.th = fma(h, ath, y.th);
+    for (int it = 0; it < kVerletIt; ++it) {
+        flow64<METRIC>(d, kk, R, w, g, Hs);
+        const double nr = fma(hh, ar + g.r, y.r), nth = fma(hh, ath + g.th, y.th);
+        const bool mv = moved2(nr, w.r, nth, w.th);
+        w.r = nr;
+        w.th = nth;
+        if (!mv) break;
+    }
+    flow64<METRIC>(d, kk, R, w, g, Hs);         // w = (Q, p+)
+    yn = State{w.r, w.th, fma(hh, g.pr, w.pr), fma(hh, g.pth, w.pth)};
+    flow64<METRIC>(d, kk, R, yn, kn, Hn);
+}
+
 __device__ __forceinline__ double sq_ratio(double e, double y, double yn, double atol, double rtol) {
     double sc = fma(rtol, fmax(fabs(y), fabs(yn)), atol);
     double q = e * rcp64(sc);
@@ -194,6 +321,40 @@ __device__ double refine_henon64(const ImageDesc& d, const KerrK& kk, const RayC
             if (!(s <= worst)) worst = s;
             z = zn;
             g = k7;
+        }
+        r_out = z.r;
+        if (worst <= 1.0) break;
+    }
+    return r_out;
+}
+
+// Henon's exact step for Gragg-Bulirsch-Stoer rays: the same sub-stepping and
+// error rule as refine_henon64, each sub-step one extrapolation macro-step of
+// the theta-system (theta integrated as a component, as its own derivative 1).
+template <int METRIC>
+__device__ double refine_henon_gbs64(const ImageDesc& d, const KerrK& kk, const RayConst& R, const State& y0,
+                                     const State& f0, double atol, double rtol) {
+    const double dth_all = kHalfPi - y0.th;
+    const double it0 = rcp64(f0.th);
+    const State g0 = State{f0.r * it0, 1.0, f0.pr * it0, f0.pth * it0};
+    auto tflow = [&](const State& z, State& g) { theta_flow64<METRIC>(d, kk, R, z, g); };
+    double r_out = y0.r;
+    for (int m = 0; m <= 6; ++m) {
+        const int nsub = 1 << m;
+        const double dl = dth_all / (double)nsub;
+        State z = y0, g = g0;
+        double worst = 0.0;
+        for (int q = 0; q < nsub; ++q) {
+            State dz, e;
+            gbs_core(z, g, dl, tflow, dz, e);
+            const State zn = add(z, dz);
+            double s = sq_ratio(e.r, z.r, zn.r, atol, rtol);
+            s += sq_ratio(e.pr, z.pr, zn.pr, atol, rtol);
+            s += sq_ratio(e.pth, z.pth, zn.pth, atol, rtol);
+            s *= (1.0 / 3.0);
+            if (!(s <= worst)) worst = s;
+            z = zn;
+            tflow(z, g);
         }
         r_out = z.r;
         if (worst <= 1.0) break;
@@ -546,7 +707,11 @@ __device__ void refine_pending(Lane& L, const SolverDesc& sol) {
         double H0;
         flow64<METRIC>(d, L.kk, L.R, L.yc, f0, H0);
         L.hmax = fmax(L.hmax, fabs(H0));
-        rc = refine_henon64<METRIC, METHOD>(d, L.kk, L.R, L.yc, f0, sol.atol, sol.rtol);
+        // the pairs and the extrapolator use their own steps, Verlet Dormand-Prince
+        if constexpr (METHOD == 3)
+            rc = refine_henon_gbs64<METRIC>(d, L.kk, L.R, L.yc, f0, sol.atol, sol.rtol);
+        else
+            rc = refine_henon64<METRIC, (METHOD <= 2 ? METHOD : 0)>(d, L.kk, L.R, L.yc, f0, sol.atol, sol.rtol);
     }
     record_crossing<METRIC>(L, rc);
     L.pend = false;
@@ -570,8 +735,15 @@ __device__ int step_ray64(Lane& L, const SolverDesc& sol) {
     if (L.h < hmin) return 3;
     State yn, kn, e;
     double Hn;
-    rk_step64<METRIC, METHOD>(d, L.kk, L.R, L.y, L.k1, L.h, yn, kn, Hn, e);
-    const double err2 = err_norm2(L.y, yn, e, sol.atol, sol.rtol);
+    if constexpr (METHOD == 4) {
+        verlet_step64<METRIC>(d, L.kk, L.R, L.y, L.k1, L.h, yn, kn, Hn);
+    } else if constexpr (METHOD == 3) {
+        gbs_step64<METRIC>(d, L.kk, L.R, L.y, L.k1, L.h, yn, kn, Hn, e);
+    } else {
+        rk_step64<METRIC, METHOD>(d, L.kk, L.R, L.y, L.k1, L.h, yn, kn, Hn, e);
+    }
+    // Verlet: fixed step, always accepted
+    const double err2 = (METHOD == 4) ? 0.0 : err_norm2(L.y, yn, e, sol.atol, sol.rtol);
     if (isnan(err2) || !isfinite(yn.r) || !isfinite(yn.th) || !isfinite(yn.pr) || !isfinite(yn.pth))
         return 4;
     if (err2 <= 1.0) {
@@ -591,12 +763,19 @@ __device__ int step_ray64(Lane& L, const SolverDesc& sol) {
         L.hmax = fmax(L.hmax, fabs(Hn));
         if (yn.r < d.r_capture) return 1;
         if (yn.r > d.r_escape) return 0;
-        const double fac = fmin(L.last_rej ? 1.0 : 10.0, fmax(0.2, step_factor(err2)));
-        L.h *= fac;
+        if constexpr (METHOD == 3) {
+            L.h *= fmin(L.last_rej ? 1.0 : 4.0, fmax(0.02, gbs_factor(err2)));
+        } else if constexpr (METHOD != 4) {
+            L.h *= fmin(L.last_rej ? 1.0 : 10.0, fmax(0.2, step_factor(err2)));
+        }
         L.last_rej = false;
     } else {
         L.rejects++;
-        L.h *= fmax(0.2, step_factor(err2));
+        if constexpr (METHOD == 3) {
+            L.h *= fmin(1.0, fmax(0.02, gbs_factor(err2)));
+        } else {
+            L.h *= fmax(0.2, step_factor(err2));
+        }
         L.last_rej = true;
     }
     return -1;
@@ -764,7 +943,7 @@ enum : int { kIdle = 0, kRun = 1, kDone = 2 };
 
 // PREC 0: FP64.  PREC 1: mixed with FP64 accumulation.  PREC 2: mixed with the
 // compensated FP32-pair accumulation.  METHOD (FP64 only): 0 Dormand-Prince,
-// 1 Cash-Karp, 2 Fehlberg.
+// 1 Cash-Karp, 2 Fehlberg, 3 Gragg-Bulirsch-Stoer, 4 Verlet.
 template <int METRIC, int PREC, int METHOD = 0>
 __device__ __forceinline__ void trace_loop(const ImageDesc* descs, int n_desc, long long total,
                                            const SolverDesc& sol, const TuneParams& tp,

@@ -130,7 +130,12 @@ def compare(orc, sc, got, ref, pix, rel=1e-9, h_abs=1e-12, h_rel=5e-2, min_same_
     g2, r2 = got["h_max"][oth], ref["h_max"][oth]
     ratio = (np.maximum(g2, r2) + h_abs) / (np.minimum(g2, r2) + h_abs)
     worst["h_max_ratio_other"] = float(ratio.max()) if ratio.size else 1.0
-    assert np.all(dh <= lim), "h_max (escaped) differs by %.3e" % dh.max()
+    if dh.size and not np.all(dh <= lim):
+        q = int(np.argmax(dh / lim))
+        idx = np.nonzero(esc)[0][q]
+        raise AssertionError("h_max (escaped) differs by %.3e at pixel %d: got %.6e ref %.6e, steps %d/%d %d/%d"
+                             % (dh[q], pix[idx], got["h_max"][idx], ref["h_max"][idx], got["steps"][idx],
+                                ref["steps"][idx], got["rejects"][idx], ref["rejects"][idx]))
     assert np.all(ratio <= h_ratio), "h_max (captured) differs by a factor %.2f" % ratio.max()
     same_steps = float(np.mean((got["steps"] == ref["steps"]) & (got["rejects"] == ref["rejects"])))
     worst["same_step_counts"] = same_steps

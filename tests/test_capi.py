@@ -75,7 +75,7 @@ BAD = [
     dict(cam__nx=0), dict(cam__alpha_min=float("inf")), dict(cam__pix_begin=-1),
     dict(cam__pix_count=10 ** 9),
     dict(s__rtol=0.0), dict(s__atol=-1.0), dict(s__max_steps=0), dict(s__escape_factor=1.0),
-    dict(s__refine=3), dict(s__horizon_eps=-0.1), dict(s__precision=5), dict(s__method=3), dict(s__method=-1),
+    dict(s__refine=3), dict(s__horizon_eps=-0.1), dict(s__precision=5), dict(s__method=5), dict(s__method=-1), dict(s__method=4),
     dict(d__max_crossings=4), dict(d__r_out=0.0),
 ]
 
@@ -92,7 +92,7 @@ def test_validation_rejects_without_gpu(over):
 def test_unsupported_and_null_arguments():
     sc = scenes.kerr_disk(16)
     L = T.lib()
-    for method in (1, 2):               # Cash-Karp and Fehlberg run in FP64 only
+    for method in (1, 2, 3, 4):         # every integrator but Dormand-Prince runs in FP64 only
         for prec in (1, 2):
             m, o, cam, s, d, out = _args(sc, s__method=method, s__precision=prec)
             assert L.tartarus_trace(C.byref(m), C.byref(o), C.byref(cam), C.byref(s), C.byref(d),
@@ -130,8 +130,8 @@ def test_batch_mixing_metric_kinds_refused_for_ck_and_f():
         m, o, cam, s, d, out = _args(sc, **({"m__kind": 1} if i == 1 else {}))
         imgs[i].metric, imgs[i].obs, imgs[i].cam, imgs[i].disk, imgs[i].out = m, o, cam, d, out
     status = (C.c_int * 2)(-7, -7)
-    for method in (1, 2):
-        s = T.solver_struct(sc.replace(method=method))
+    for method in (1, 2, 3, 4):
+        s = T.solver_struct(sc.replace(method=method, h0=0.01))
         for fn in (T.lib().tartarus_trace_batch, T.lib().tartarus_trace_batch_noalloc):
             assert fn(imgs, 2, C.byref(s), None, status, None) == T.TT_EUNSUPPORTED
             assert list(status) == [-7, -7]          # refused before any image was looked at
