@@ -78,7 +78,7 @@ def parse():
                    help="integrator of the FP64 run (default: Dormand-Prince, the headline)")
     p.add_argument("--no-pairs", action="store_true",
                    help="skip the objects of the other four integrators in the default line")
-    p.add_argument("--workload", default="kerr_disk", choices=["kerr_disk", "batch", "table"],
+    p.add_argument("--workload", default="kerr_disk", choices=["kerr_disk", "batch", "table", "e3", "e5", "osiris"],
                    help="kerr_disk: the 1024^2 headline image (default); batch: 64 uneven images in one "
                         "persistent launch, replayed from a CUDA graph; table: the 4096^2 tabulated-metric image")
     return p.parse_args()
@@ -420,7 +420,7 @@ def run_workload(args):
         cfg = {"workload": name, "images": 64, "rays": rays, "res": [min(s.nx for s in imgs), max(s.nx for s in imgs)],
                "rtol": imgs[0].rtol, "precision": "mixed_pair", "launch": "CUDA graph replay of one batch call"}
         direct = lambda: T.trace_batch(imgs, outs)
-    else:
+    elif args.workload == "table":
         sc = scenes.table_kerr_with_nodes(args.n if args.n != 1024 else 4096)
         table = T.Table(sc.table, sc.r_min, sc.r_max)
         out = T.alloc_outputs(sc.npix)
@@ -432,6 +432,24 @@ def run_workload(args):
         dtype = "f64"
         cfg = {"workload": name, "nx": sc.nx, "ny": sc.ny, "a": sc.a, "table": [512, 256], "rtol": sc.rtol,
                "precision": "fp64"}
+        direct = None
+    else:
+        # the paper's own scenes: Fig. 3 (e3), Table 1 (e5), the OSIRIS shadow of Figs. 5-6
+        make = {"e3": scenes.kerr_e3, "e5": scenes.schwarzschild_e5, "osiris": scenes.osiris_scene}
+        sc = make[args.workload](args.n).replace(method=METHODS[args.method])
+        if args.method == "verlet":
+            sc = sc.replace(h0=VERLET_H, horizon_eps=VERLET_EPS)
+        out = T.alloc_outputs(sc.npix)
+        rays = sc.npix
+        step = lambda: T.trace(sc, out=out, stream=stream)
+        launches_per_step = 1
+        outs = [out]
+        name = sc.name
+        dtype = "f64"
+        cfg = {"workload": name, "nx": sc.nx, "ny": sc.ny, "a": sc.a, "r_obs": sc.r_obs,
+               "theta_obs_deg": round(sc.theta_obs * 180.0 / math.pi, 6),
+               "field": [sc.alpha_min, sc.alpha_max], "disk": bool(sc.disk_enabled), "doppler": sc.doppler,
+               "rtol": sc.rtol, "integrator": args.method, "precision": "fp64"}
         direct = None
     for k in range(max(args.warmup, 0)):
         flush.fill_(k & 0xFF)
@@ -462,9 +480,17 @@ def run_workload(args):
     kern_ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
     attempts = int(sum(o["steps"].sum().item() + o["rejects"].sum().item() for o in outs))
     if rank == 0:
+        fpu = None
         if args.workload == "batch":
-            flops = FLOPS_PER_STEP_F32 * attempts
+            fpu, flops = FLOPS_PER_STEP_F32, FLOPS_PER_STEP_F32 * attempts
             peak, unit = FP32_PEAK_TFLOPS, "TFLOP/s"
+            work = "FP32 Dormand-Prince step attempt (FP64 side work not counted)"
+            src = "FP32 pipe: 152 SMs x 2070 MHz x 128 FFMA/clk (derived)"
+        elif args.workload in ("e3", "e5", "osiris") and sc.method in FLOPS_PER_STEP_METHOD:
+            fpu = FLOPS_PER_STEP_METHOD[sc.method]
+            flops, peak, unit = fpu * attempts, FP64_PEAK_TFLOPS, "TFLOP/s"
+            work = "%s step attempt" % args.method
+            src = "FP64 pipe: 152 SMs x 2070 MHz x 2 DFMA/clk (derived)"
         else:
             flops, peak, unit = None, FP64_PEAK_TFLOPS, "TFLOP/s"
         line = {"metric": METRIC, "value": world * rays * args.steps / (total_ms / 1e3), "unit": UNIT,
@@ -476,9 +502,11 @@ def run_workload(args):
         if flops is not None:
             ach = flops / (kern_ms / 1e3) / 1e12
             line["roofline"] = {"bound": "alu", "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak,
-                                "traffic": None, "flops_per_unit": FLOPS_PER_STEP_F32,
-                                "unit_of_work": "FP32 Dormand-Prince step attempt (FP64 side work not counted)",
-                                "peak_source": "FP32 pipe: 152 SMs x 2070 MHz x 128 FFMA/clk (derived)"}
+                                "traffic": None, "flops_per_unit": fpu, "unit_of_work": work,
+                                "peak_source": src}
+        if args.workload in ("e3", "e5", "osiris"):
+            # the paper's hardware-independent figure: wall time per photon per integration step
+            line["ns_per_photon_step"] = total_ms / args.steps * 1e6 / max(attempts, 1)
         if direct is not None:
             direct()
             torch.cuda.synchronize()

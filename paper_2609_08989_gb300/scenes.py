@@ -107,7 +107,27 @@ def kerr_disk_mixed(n: int = 2048) -> Scene:
                                        rtol=MIXED_RTOL, atol=MIXED_RTOL)
 
 
+def kerr_e3(n: int = 1024, doppler: int = 1) -> Scene:
+    """Paper Sec. 4.2, Fig. 3: Kerr a = 0.5 with a thin disk seen from D = 100 M at
+    85 deg, with (panel a) or without (panel b) the Doppler factor.  The paper gives
+    no field or disk edge: the field [-32, 32]^2 M holds the whole disk out to 30 M
+    (its image spans |alpha| <= 30.3 M)."""
+    return Scene(name="kerr_a0.5_i85_d100_disk_%d%s" % (n, "" if doppler else "_nodoppler"), a=0.5,
+                 r_obs=100.0, theta_obs=deg(85.0), nx=n, ny=n, alpha_min=-32.0, alpha_max=32.0,
+                 beta_min=-32.0, beta_max=32.0, disk_enabled=1, r_in=0.0, r_out=30.0, mdot=1.0,
+                 max_crossings=3, doppler=doppler)
+
+
+def schwarzschild_e5(n: int = 1024) -> Scene:
+    """Paper Sec. 4.3, Table 1: Schwarzschild with a thin disk seen from D = 100 M.
+    The paper gives no inclination, field or tolerance: those of the Fig. 3 scene
+    (85 deg, [-32, 32]^2 M, disk to 30 M) and the tolerance of its Fig. 1 tests (1e-10)."""
+    return kerr_e3(n).replace(name="schwarzschild_i85_d100_disk_%d" % n, a=0.0)
+
+
 def osiris_scene(n: int = 1024) -> Scene:
+    """Paper Sec. 4.3, Figs. 5-6: the OSIRIS calibration shadow, Kerr a = 0.98, an
+    equatorial observer at 1000 M, field [-8, 8]^2 M, no disk (tolerance not given: 1e-10)."""
     return Scene(name="osiris_a0.98_i90_%d" % n, a=0.98, theta_obs=deg(90.0), nx=n, ny=n,
                  alpha_min=-8.0, alpha_max=8.0, beta_min=-8.0, beta_max=8.0)
 
