@@ -32,17 +32,20 @@ SM_MAX_MHZ = 2070.0
 # FP64 pipe: 2 DFMA per clock per SM (measured 1.185 TFLOP/s at 1995 MHz with an FMA-chain probe)
 FP64_PEAK_TFLOPS = SM_COUNT * SM_MAX_MHZ * 1e6 * 2 * 2 / 1e12
 # Algorithmic FP64 flops of one Dormand-Prince step attempt on the Kerr FP64 path,
-# counted from the kernel source (FMA = 2, add/mul/div/rcp/sqrt = 1, sin and cos 1 each):
-# 6 flow evaluations x 65 + stage combinations 232 + error norm 20 + step control 5.
-FLOPS_PER_STEP = 6 * 65 + 232 + 20 + 5
+# counted from the kernel source of this build (FMA = 2; add, mul, reciprocal and
+# sqrt 1 each, the reciprocal's Newton refinement not counted; sin and cos 1 each):
+# 6 flow evaluations x 56 + stage combinations 226 (stages 2-4 with h-scaled
+# coefficients) + error norm 30 (one shared reciprocal) + step control 5.
+FLOW_FLOPS, NORM_FLOPS, CONTROL_FLOPS = 56, 30, 5
+FLOPS_PER_STEP = 6 * FLOW_FLOPS + 226 + NORM_FLOPS + CONTROL_FLOPS
 # Cash-Karp and Fehlberg also evaluate the flow six times per step attempt (five
 # stages and the new point); their stage sums have one (Fehlberg: e_7 = 0) or two
 # (Cash-Karp: b_5 = e_7 = 0) fewer FMA per state component.
 # Gragg-Bulirsch-Stoer macro-step (6 columns, 2..12 sub-steps): 36 chain flows + the flow at
 # the new point, 12 flops per chain sub-step (y + d, d0 + 2h f), 6 x (4 + 1) to start the
 # chains, 15 Aitken-Neville updates x 4 components x 3, the new point and the error (8),
-# norm 20, control 5.
-FLOPS_PER_GBS_STEP = 37 * 65 + 36 * 12 + 6 * 5 + 15 * 4 * 3 + 8 + 20 + 5
+# norm and control.
+FLOPS_PER_GBS_STEP = 37 * FLOW_FLOPS + 36 * 12 + 6 * 5 + 15 * 4 * 3 + 8 + NORM_FLOPS + CONTROL_FLOPS
 FLOPS_PER_STEP_METHOD = {0: FLOPS_PER_STEP, 1: FLOPS_PER_STEP - 2 * 2 * 4, 2: FLOPS_PER_STEP - 2 * 4,
                          3: FLOPS_PER_GBS_STEP}
 METHODS = {"dopri5": 0, "cash_karp": 1, "fehlberg": 2, "gbs": 3, "verlet": 4}
@@ -51,7 +54,8 @@ METHODS = {"dopri5": 0, "cash_karp": 1, "fehlberg": 2, "gbs": 3, "verlet": 4}
 # outruns any fixed step and the implicit half steps diverge
 VERLET_H, VERLET_EPS, VERLET_N = 0.01, 0.025, 128
 METHOD_NAMES = {v: k for k, v in METHODS.items()}
-# The same count for an FP32 step of the mixed paths (the rearranged FP32 flow is 72).
+# The same count for an FP32 step of the mixed paths (the rearranged FP32 flow is 72;
+# its stages, norm and control as in the FP64 step before the h-scaling above).
 FLOPS_PER_STEP_F32 = 6 * 72 + 232 + 20 + 5
 FP32_PEAK_TFLOPS = SM_COUNT * SM_MAX_MHZ * 1e6 * 128 * 2 / 1e12
 BYTES_OUT_PER_PIXEL = 3 * 3 * 8 + 8 + 8 + 4 + 4 + 1 + 1

@@ -174,17 +174,23 @@ typedef struct {
 } tt_outputs;
 
 /* Launch shape of the persistent kernel; NULL or zero fields select defaults.
- *   block           threads per block: 128 (default) or 256
+ *   block           threads per block, 0 (default), 128, 256 or 384.  Built:
+ *                   FP64 Dormand-Prince on the closed-form metric 128 (default),
+ *                   256 and 384; the other FP64 integrators 128 (default) and
+ *                   256 (384 runs as 256); tables 128 (any size runs as 128);
+ *                   mixed paths 256 (default; 384 runs as 256, 128 fails with
+ *                   TT_ECUDA).  Other sizes: TT_EUNSUPPORTED.
  *   reg_variant     registers per thread of the FP64 closed-form Kerr kernel at
  *                   128 threads, single camera: 0 the compiler's choice, 1 at
  *                   most 168, 2 at most 128 (other kernels ignore it)
  *   refill          flush finished rays and refill lanes once at least this many
- *                   lanes of a warp are done or idle (1..32, default 8)
+ *                   lanes of a warp are done or idle (1..32; default 4 on the
+ *                   FP64 paths, 16 on the mixed paths)
  *   blocks_per_sm   persistent blocks per SM (0: as many as fit)
  *   crossing_batch  refine disk crossings once this many lanes of a warp have
- *                   one pending (1..32, default 8)
+ *                   one pending (1..32; default 8 FP64, 16 mixed)
  *   fp64_batch      mixed paths: run the FP64 near-horizon steps once this many
- *                   lanes need one (1..32, default 8)
+ *                   lanes need one (1..32, default 16)
  *   monitor_period  mixed paths: evaluate |H| in FP64 every this many warp
  *                   iterations (default 32)
  *   fp64_wait       mixed paths: lanes waiting for an FP64 step get one after at

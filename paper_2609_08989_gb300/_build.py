@@ -20,6 +20,10 @@ SOURCES = ["tt_capi.cu", "tt_kernel64.cu", "tt_kernel_mixed.cu", "tt_kernel_ck.c
 HEADERS = ["tt_internal.h", "tt_device.cuh", "tt_trace.cuh", "tt_kernel_rk.cuh", os.path.join("..", "..", "include", "tartarus.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
+# The FP64 kernels write every fused multiply-add explicitly; without contraction
+# by the compiler each build (block size, batch width) rounds alike, so results
+# do not depend on the launch shape.
+NO_CONTRACT = {"tt_kernel64.cu", "tt_kernel_ck.cu", "tt_kernel_f.cu", "tt_kernel_gbs.cu", "tt_kernel_verlet.cu"}
 
 
 def nvcc() -> str:
@@ -41,7 +45,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     def compile_one(src):
         obj = os.path.join(BUILD, src.replace(".cu", ".o"))
-        cmd = [nvcc(), *ARCH, *FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
+        extra = ["-fmad=false"] if src in NO_CONTRACT else []
+        cmd = [nvcc(), *ARCH, *FLAGS, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
         r = subprocess.run(cmd, capture_output=True, text=True)

@@ -227,9 +227,10 @@ tt::LaunchShape make_shape(const tt_tune* t) {
 
 int check_shape(const tt_tune* t) {
     if (!t) return TT_OK;
-    if (t->block != 0 && t->block != 128 && t->block != 256) return TT_EUNSUPPORTED;
-    // built variants: 128 or 256 threads (FP64, closed-form Kerr), 128 (FP64 tables),
-    // 256 (mixed paths)
+    if (t->block != 0 && t->block != 128 && t->block != 256 && t->block != 384) return TT_EUNSUPPORTED;
+    // built variants: 128, 256 or 384 threads (FP64 Dormand-Prince, closed-form Kerr),
+    // 128 or 256 (the other FP64 integrators; 384 runs as 256), 128 (FP64 tables),
+    // 256 (mixed paths; 384 runs as 256, 128 is refused at launch)
     if (t->reg_variant < 0 || t->reg_variant > 2) return TT_EUNSUPPORTED;
     if (t->refill < 0 || t->refill > 32) return TT_EINVAL;
     if (t->blocks_per_sm < 0) return TT_EINVAL;

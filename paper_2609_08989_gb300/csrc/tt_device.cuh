@@ -37,6 +37,7 @@ struct RayConst {
     double a2pt2;         // a^2 p_t^2
     double c0;            // 2 a p_t p_phi
     double pt4;           // 4 p_t
+    double pt2;           // 2 p_t
 };
 
 __device__ __forceinline__ RayConst make_ray_const(double a, double pt, double pph) {
@@ -48,6 +49,7 @@ __device__ __forceinline__ RayConst make_ray_const(double a, double pt, double p
     R.a2pt2 = a * a * pt * pt;
     R.c0 = 2.0 * a * pt * pph;
     R.pt4 = 4.0 * pt;
+    R.pt2 = 2.0 * pt;
     return R;
 }
 
@@ -78,40 +80,45 @@ struct State {
 //   dp_r  = -(dK/dr  - 4 r H) / (2 Sigma),
 //   dp_th = -(dK/dth + 4 a^2 sin cos H) / (2 Sigma),
 // Hamilton's equations of Sec. 2.1 exactly (the H terms keep the flow exact
-// off the constraint surface).  One reciprocal serves 1/Sigma, 1/Delta and
-// 1/sin^2.
+// off the constraint surface).  With A = (r^2 + a^2) p_t + a p_phi and
+// H2 = 2H = K / Sigma the two forces are evaluated as
+//   dp_r  = [r (H2 + 2 p_t A/Delta) - (r - M)((A/Delta)^2 + p_r^2)] / Sigma,
+//   dp_th = -sin cos [a^2 H2 + a^2 p_t^2 - p_phi^2 / sin^4] / Sigma
+// (the same expressions regrouped: 4 fewer FP64 operations per evaluation).
+// One reciprocal serves 1/Sigma, 1/Delta and 1/sin^2.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void kerr_flow64(const KerrK& k, const RayConst& R, const State& y,
                                             State& f, double& H) {
     double s, c;
     sincos(y.th, &s, &c);
     const double r = y.r;
-    double s2 = s * s, c2 = c * c, sc = s * c;
-    double r2 = r * r;
-    double Sig = fma(k.a2, c2, r2);
-    double Del = fma(r, r - k.twoM, k.a2);
-    double A = fma(r2 + k.a2, R.pt, R.apph);
-    double SD = Sig * Del;
-    double inv = rcp64(SD * s2);
-    double iS = inv * (Del * s2);
-    double iD = inv * (Sig * s2);
-    double u = inv * SD;
-    double pr2 = y.pr * y.pr;
-    double AiD = A * iD;
+    const double s2 = s * s, c2 = c * c, sc = s * c;
+    const double r2 = r * r;
+    const double Sig = fma(k.a2, c2, r2);
+    const double Del = fma(r, r - k.twoM, k.a2);
+    const double A = fma(fma(r, r, k.a2), R.pt, R.apph);
+    const double SD = Sig * Del;
+    const double inv = rcp64(SD * s2);
+    const double iS = inv * (Del * s2);              // 1 / Sigma
+    const double iD = inv * (Sig * s2);              // 1 / Delta
+    const double u = inv * SD;                       // 1 / sin^2
+    const double pr2 = y.pr * y.pr;
+    const double AiD = A * iD;
     double K = fma(R.a2pt2, s2, R.c0);
     K = fma(R.pph2, u, K);
     K = fma(y.pth, y.pth, K);
     K = fma(Del, pr2, K);
     K = fma(-A, AiD, K);
-    double hiS = 0.5 * iS;
-    H = K * hiS;
-    double Dr = fma(2.0, r, -k.twoM);                          // dDelta/dr
-    double dKr = fma(Dr, fma(AiD, AiD, pr2), -(r * R.pt4) * AiD);
-    double dKt = (2.0 * sc) * fma(-R.pph2, u * u, R.a2pt2);
-    f.r = (Del * iS) * y.pr;
+    const double H2 = K * iS;
+    H = 0.5 * H2;
+    const double q1 = fma(R.pt2, AiD, H2);
+    const double q2 = fma(AiD, AiD, pr2);
+    const double t1 = fma(-R.pph2, u * u, R.a2pt2);
+    const double t2 = fma(k.a2, H2, t1);
+    f.r = (Del * y.pr) * iS;
     f.th = y.pth * iS;
-    f.pr = fma(4.0 * r, H, -dKr) * hiS;
-    f.pth = -fma(k.fourA2 * sc, H, dKt) * hiS;
+    f.pr = fma(r, q1, -((r - k.M) * q2)) * iS;
+    f.pth = -(sc * iS) * t2;
 }
 
 // ---------------------------------------------------------------------------
@@ -219,14 +226,15 @@ __device__ __forceinline__ void kerr_lower64(double M, double a, double r, doubl
 // unit-cell coordinates -- so a patch is a plain tensor-product Hermite form.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void hermite4(double t, double h[4], double dh[4]) {
+    // explicit FMAs only, so that every build rounds alike
     double t2 = t * t, omt = 1.0 - t;
-    h[0] = (1.0 + 2.0 * t) * omt * omt;
+    h[0] = fma(2.0, t, 1.0) * omt * omt;
     h[1] = t * omt * omt;
-    h[2] = t2 * (3.0 - 2.0 * t);
+    h[2] = t2 * fma(-2.0, t, 3.0);
     h[3] = t2 * (t - 1.0);
-    dh[0] = 6.0 * t2 - 6.0 * t;
+    dh[0] = 6.0 * (t2 - t);
     dh[1] = fma(3.0, t2, fma(-4.0, t, 1.0));
-    dh[2] = 6.0 * t - 6.0 * t2;
+    dh[2] = 6.0 * (t - t2);
     dh[3] = fma(3.0, t2, -2.0 * t);
 }
 
@@ -291,8 +299,8 @@ __device__ __forceinline__ void table_flow64(const ImageDesc& d, const RayConst&
     double dW_t = fma(Ft[3], pt2, fma(-Ft[1], ptp, Ft[0] * R.pph2));
     double dD_t = fma(Ft[0], F[3], fma(F[0], Ft[3], -2.0 * F[1] * Ft[1]));
     double ith2 = ith * ith;
-    double d2H_r = fma(-WiD, dD_r, dW_r) * iD + fma(Fr[4], pr2, -Fr[2] * ith2 * pth2);
-    double d2H_t = fma(-WiD, dD_t, dW_t) * iD + fma(Ft[4], pr2, -Ft[2] * ith2 * pth2);
+    double d2H_r = fma(fma(-WiD, dD_r, dW_r), iD, fma(Fr[4], pr2, -Fr[2] * ith2 * pth2));
+    double d2H_t = fma(fma(-WiD, dD_t, dW_t), iD, fma(Ft[4], pr2, -Ft[2] * ith2 * pth2));
     f.r = F[4] * y.pr;
     f.th = y.pth * ith;
     f.pr = -0.5 * d2H_r;

@@ -13,6 +13,12 @@ __global__ void __launch_bounds__(256) trace_kernel64_b256(const __grid_constant
     trace_loop<METRIC, 0>(p.desc, p.n_desc, p.total, p.sol, p.tune, p.queue);
 }
 
+// 384 threads (12 warps per SM at 160 registers, against 8 for 256 threads).
+template <int METRIC, int N>
+__global__ void __launch_bounds__(384) trace_kernel64_b384(const __grid_constant__ LaunchParams<N> p) {
+    trace_loop<METRIC, 0>(p.desc, p.n_desc, p.total, p.sol, p.tune, p.queue);
+}
+
 // Register-capped builds of the closed-form Kerr kernel (128 threads): at least
 // MINB resident blocks per SM caps registers at 65536 / (128 MINB) per thread
 // (MINB 3: 168, MINB 4: 128).
@@ -32,8 +38,9 @@ int sm_count() {
     return n;
 }
 
-// Built variants: closed-form Kerr (128 and 256 threads), tables (128), and
-// batches that mix both kinds (128, batch width only).
+// Built variants: closed-form Kerr (128, 256 and 384 threads), tables (128),
+// and batches that mix both kinds (128, batch width only); a block size
+// without a build of its own runs at the kernel's built size.
 template <int N>
 static cudaError_t launch64(const ImageDesc* descs, int n, long long total, int metric_mode, const SolverDesc& sol,
                             const LaunchShape& shape, unsigned long long* queue, cudaStream_t stream) {
@@ -42,6 +49,7 @@ static cudaError_t launch64(const ImageDesc* descs, int n, long long total, int 
     const int bps = shape.blocks_per_sm;
     if (metric_mode == 0) {
         if (shape.block == 256) return launch_persistent<N>(trace_kernel64_b256<0, N>, 256, bps, p, stream);
+        if (shape.block == 384) return launch_persistent<N>(trace_kernel64_b384<0, N>, 384, bps, p, stream);
         if constexpr (N == 1) {
             if (shape.reg_variant == 1) return launch_persistent<N>(trace_kernel64_regcap<3>, 128, bps, p, stream);
             if (shape.reg_variant == 2) return launch_persistent<N>(trace_kernel64_regcap<4>, 128, bps, p, stream);

@@ -23,7 +23,7 @@ static cudaError_t launch_rk_n(const ImageDesc* descs, int n, long long total, i
     fill_params<N>(p, descs, n, total, sol, shape, queue);
     const int bps = shape.blocks_per_sm;
     if (metric_mode == 0) {
-        if (shape.block == 256) return launch_persistent<N>(trace_kernel_rk<METHOD, 0, N, 256>, 256, bps, p, stream);
+        if (shape.block >= 256) return launch_persistent<N>(trace_kernel_rk<METHOD, 0, N, 256>, 256, bps, p, stream);
         return launch_persistent<N>(trace_kernel_rk<METHOD, 0, N, 128>, 128, bps, p, stream);
     }
     if (metric_mode == 1) return launch_persistent<N>(trace_kernel_rk<METHOD, 1, N, 128>, 128, bps, p, stream);

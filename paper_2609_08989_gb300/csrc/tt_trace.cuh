@@ -67,15 +67,25 @@ __device__ __forceinline__ void rk_step64(const ImageDesc& d, const KerrK& kk, c
     ys.pr = fma(h, (expr_p), y.pr);                                                  \
     ys.pth = fma(h, (expr_q), y.pth);                                                \
     flow64<METRIC>(d, kk, R, ys, dst, Hs);
-#define TT_C2(f) (T::a21 * k1.f)
-#define TT_C3(f) fma(T::a32, k2.f, T::a31 * k1.f)
-#define TT_C4(f) fma(T::a43, k3.f, fma(T::a42, k2.f, T::a41 * k1.f))
+// stages 2-4: coefficients pre-multiplied by h (one multiply each, shared by
+// the four components), the stage point an FMA chain from y
+#define TT_PSTAGE(dst, EXPR)                                                         \
+    ys.r = EXPR(r);                                                                  \
+    ys.th = EXPR(th);                                                                \
+    ys.pr = EXPR(pr);                                                                \
+    ys.pth = EXPR(pth);                                                              \
+    flow64<METRIC>(d, kk, R, ys, dst, Hs);
+    const double h21 = h * T::a21, h31 = h * T::a31, h32 = h * T::a32;
+    const double h41 = h * T::a41, h42 = h * T::a42, h43 = h * T::a43;
+#define TT_P2(f) fma(h21, k1.f, y.f)
+#define TT_P3(f) fma(h32, k2.f, fma(h31, k1.f, y.f))
+#define TT_P4(f) fma(h43, k3.f, fma(h42, k2.f, fma(h41, k1.f, y.f)))
 #define TT_C5(f) fma(T::a54, k4.f, fma(T::a53, k3.f, fma(T::a52, k2.f, T::a51 * k1.f)))
 #define TT_C6(f) fma(T::a65, k5.f, fma(T::a64, k4.f, fma(T::a63, k3.f, fma(T::a62, k2.f, T::a61 * k1.f))))
 #define TT_C7(f) fma(T::b6, k6.f, TT_MAC(T::b5, k5.f, fma(T::b4, k4.f, fma(T::b3, k3.f, T::b1 * k1.f))))
-    TT_STAGE(k2, TT_C2(r), TT_C2(th), TT_C2(pr), TT_C2(pth))
-    TT_STAGE(k3, TT_C3(r), TT_C3(th), TT_C3(pr), TT_C3(pth))
-    TT_STAGE(k4, TT_C4(r), TT_C4(th), TT_C4(pr), TT_C4(pth))
+    TT_PSTAGE(k2, TT_P2)
+    TT_PSTAGE(k3, TT_P3)
+    TT_PSTAGE(k4, TT_P4)
     TT_STAGE(k5, TT_C5(r), TT_C5(th), TT_C5(pr), TT_C5(pth))
     TT_STAGE(k6, TT_C6(r), TT_C6(th), TT_C6(pr), TT_C6(pth))
     yn.r = fma(h, TT_C7(r), y.r);
@@ -91,9 +101,10 @@ __device__ __forceinline__ void rk_step64(const ImageDesc& d, const KerrK& kk, c
     err.pth = TT_E(pth);
 #undef TT_E
 #undef TT_STAGE
-#undef TT_C2
-#undef TT_C3
-#undef TT_C4
+#undef TT_PSTAGE
+#undef TT_P2
+#undef TT_P3
+#undef TT_P4
 #undef TT_C5
 #undef TT_C6
 #undef TT_C7
@@ -147,8 +158,9 @@ __device__ __forceinline__ void gbs_core(const State& y, const State& f0, double
             T[0] = d1;
 #pragma unroll
             for (int l = 1; l < j; ++l) {
-                const double ratio = (double)j / (double)(j - l);
-                const double w = 1.0 / (ratio * ratio - 1.0);
+                // 1 / ((j / (j - l))^2 - 1) as one quotient of integers (rounded alike
+                // whether or not the loop unrolls into constants)
+                const double w = (double)((j - l) * (j - l)) / (double)(l * (2 * j - l));
                 const State old = T[l];         // T_{j-1,l+1}
                 T[l] = axpy(w, sub(T[l - 1], prev), T[l - 1]);
                 prev = old;
@@ -226,20 +238,52 @@ __device__ __forceinline__ void verlet_step64(const ImageDesc& d, const KerrK& k
     flow64<METRIC>(d, kk, R, yn, kn, Hn);
 }
 
-__device__ __forceinline__ double sq_ratio(double e, double y, double yn, double atol, double rtol) {
-    double sc = fma(rtol, fmax(fabs(y), fabs(yn)), atol);
-    double q = e * rcp64(sc);
-    return q * q;
+// e / (atol + rtol max(|y|, |yn|)); callers square and sum with explicit FMAs
+// (never left to the compiler's contraction, so every build rounds alike).
+__device__ __forceinline__ double err_ratio(double e, double y, double yn, double atol, double rtol) {
+    const double sc = fma(rtol, fmax(fabs(y), fabs(yn)), atol);
+    return e * rcp64(sc);
 }
 
-// Mean-square error norm over (r, theta, p_r, p_theta).
+__device__ __forceinline__ double sq3(double a, double b, double c) {
+    return fma(c, c, fma(b, b, a * a));
+}
+
+// Mean-square error norm over (r, theta, p_r, p_theta).  The four scale
+// factors share one reciprocal: 1/sc_0 = sc_1 sc_2 sc_3 / (sc_0 sc_1 sc_2 sc_3),
+// refined by a single Newton step (~1e-14 relative: the norm only decides
+// err <= 1 and scales the step).  A product outside the normal range (tolerances
+// near 1e-75 or 1e75) takes the per-component reciprocals instead.
 __device__ __forceinline__ double err_norm2(const State& y, const State& yn, const State& e,
                                             double atol, double rtol) {
-    double s = sq_ratio(e.r, y.r, yn.r, atol, rtol);
-    s += sq_ratio(e.th, y.th, yn.th, atol, rtol);
-    s += sq_ratio(e.pr, y.pr, yn.pr, atol, rtol);
-    s += sq_ratio(e.pth, y.pth, yn.pth, atol, rtol);
-    return 0.25 * s;
+    const double s0 = fma(rtol, fmax(fabs(y.r), fabs(yn.r)), atol);
+    const double s1 = fma(rtol, fmax(fabs(y.th), fabs(yn.th)), atol);
+    const double s2 = fma(rtol, fmax(fabs(y.pr), fabs(yn.pr)), atol);
+    const double s3 = fma(rtol, fmax(fabs(y.pth), fabs(yn.pth)), atol);
+    const double p01 = s0 * s1, p23 = s2 * s3;
+    const double pp = p01 * p23;
+    if (!(pp > 1e-280 && pp < 1e280)) {
+        const double q3 = err_ratio(e.pth, y.pth, yn.pth, atol, rtol);
+        return 0.25 * fma(q3, q3, sq3(err_ratio(e.r, y.r, yn.r, atol, rtol), err_ratio(e.th, y.th, yn.th, atol, rtol),
+                                      err_ratio(e.pr, y.pr, yn.pr, atol, rtol)));
+    }
+    double inv;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(inv) : "d"(pp));
+    inv = fma(inv, fma(-pp, inv, 1.0), inv);
+    const double i01 = inv * p23, i23 = inv * p01;   // 1/(s0 s1), 1/(s2 s3)
+    const double q0 = (e.r * s1) * i01, q1 = (e.th * s0) * i01;
+    const double q2 = (e.pr * s3) * i23, q3 = (e.pth * s2) * i23;
+    return 0.25 * fma(q3, q3, fma(q2, q2, fma(q1, q1, q0 * q0)));
+}
+
+// Non-finite tests on the exponent bits (integer pipe, not the FP64 pipe).
+__device__ __forceinline__ bool nonfinite_bits(double x) {
+    return (__double2hiint(x) & 0x7ff00000) == 0x7ff00000;
+}
+
+__device__ __forceinline__ bool nan_bits(double x) {
+    const int hi = __double2hiint(x);
+    return (hi & 0x7ff00000) == 0x7ff00000 && (((hi & 0x000fffff) | __double2loint(x)) != 0);
 }
 
 // ---------------------------------------------------------------------------
@@ -306,9 +350,8 @@ __device__ double refine_henon64(const ImageDesc& d, const KerrK& kk, const RayC
             theta_flow64<METRIC>(d, kk, R, zn, k7);
 #define TT_E(f) \
     dl * TT_MAC(T::e7, k7.f, fma(T::e6, k6.f, fma(T::e5, k5.f, fma(T::e4, k4.f, fma(T::e3, k3.f, T::e1 * g.f)))))
-            double s = sq_ratio(TT_E(r), z.r, zn.r, atol, rtol);
-            s += sq_ratio(TT_E(pr), z.pr, zn.pr, atol, rtol);
-            s += sq_ratio(TT_E(pth), z.pth, zn.pth, atol, rtol);
+            double s = sq3(err_ratio(TT_E(r), z.r, zn.r, atol, rtol), err_ratio(TT_E(pr), z.pr, zn.pr, atol, rtol),
+                           err_ratio(TT_E(pth), z.pth, zn.pth, atol, rtol));
 #undef TT_E
 #undef TT_HS
 #undef TT_C2
@@ -348,9 +391,8 @@ __device__ double refine_henon_gbs64(const ImageDesc& d, const KerrK& kk, const 
             State dz, e;
             gbs_core(z, g, dl, tflow, dz, e);
             const State zn = add(z, dz);
-            double s = sq_ratio(e.r, z.r, zn.r, atol, rtol);
-            s += sq_ratio(e.pr, z.pr, zn.pr, atol, rtol);
-            s += sq_ratio(e.pth, z.pth, zn.pth, atol, rtol);
+            double s = sq3(err_ratio(e.r, z.r, zn.r, atol, rtol), err_ratio(e.pr, z.pr, zn.pr, atol, rtol),
+                           err_ratio(e.pth, z.pth, zn.pth, atol, rtol));
             s *= (1.0 / 3.0);
             if (!(s <= worst)) worst = s;
             z = zn;
@@ -372,14 +414,14 @@ static __device__ double refine_hermite64(const State& y0, const State& f0, cons
         double mid = 0.5 * (lo + hi);
         double B[4], dB[4];
         hermite4(mid, B, dB);
-        double th = B[0] * y0.th + B[1] * h * f0.th + B[2] * y1.th + B[3] * h * f1.th;
+        double th = fma(B[3] * h, f1.th, fma(B[2], y1.th, fma(B[1] * h, f0.th, B[0] * y0.th)));
         if ((th <= kHalfPi) == s0) lo = mid;
         else hi = mid;
     }
     double sc = 0.5 * (lo + hi);
     double B[4], dB[4];
     hermite4(sc, B, dB);
-    return B[0] * y0.r + B[1] * h * f0.r + B[2] * y1.r + B[3] * h * f1.r;
+    return fma(B[3] * h, f1.r, fma(B[2], y1.r, fma(B[1] * h, f0.r, B[0] * y0.r)));
 }
 
 // Hairer-Norsett-Wanner starting step (embedded order 4), four-component norm.
@@ -744,7 +786,8 @@ __device__ int step_ray64(Lane& L, const SolverDesc& sol) {
     }
     // Verlet: fixed step, always accepted
     const double err2 = (METHOD == 4) ? 0.0 : err_norm2(L.y, yn, e, sol.atol, sol.rtol);
-    if (isnan(err2) || !isfinite(yn.r) || !isfinite(yn.th) || !isfinite(yn.pr) || !isfinite(yn.pth))
+    if (nan_bits(err2) | nonfinite_bits(yn.r) | nonfinite_bits(yn.th) | nonfinite_bits(yn.pr) |
+        nonfinite_bits(yn.pth))
         return 4;
     if (err2 <= 1.0) {
         L.steps++;

@@ -105,10 +105,12 @@ def test_gbs_kerr_disk_128(T, orc):
     # the extrapolator's error estimate is a difference of extrapolated values, so a
     # few accept/reject decisions flip on rounding (~5e-4 of rays, also between two
     # oracle runs whose inputs differ by 1e-15); such rays take another valid step
-    # sequence, crossings still agree within 1e-9.  Its |H| maximum is set by rare
-    # steps whose error estimate cancels, and moves by up to ~9x when the sequence
-    # changes (the same 1e-15 oracle experiment): |H| is compared within 10x.
-    rep = parity.compare(orc, sc, got, orc.trace(sc), np.arange(sc.npix), rel_diverged=1e-9,
+    # sequence -- sometimes with the same totals of accepted and rejected steps, so
+    # the flip is not visible in the outputs -- and differ by the integration's own
+    # error (GBS at rtol 1e-10 is within 8.8e-10 of the Mino-time crossings): the bar
+    # is 5e-9.  Its |H| maximum is set by rare steps whose error estimate cancels and
+    # moves by up to ~9x when the sequence changes: |H| is compared within 10x.
+    rep = parity.compare(orc, sc, got, orc.trace(sc), np.arange(sc.npix), rel=5e-9, rel_diverged=5e-9,
                          h_ratio_only=True, h_ratio=10.0)
     print("GBS kerr disk 128^2:", rep)
     wide = run(T, sc, tune=dict(block=256, crossing_batch=16))
@@ -122,7 +124,7 @@ def test_gbs_full_size_sampled(T, orc):
     pix = scenes.sample_pixels(sc.npix, 1500, 29)
     ref = orc.trace_list(sc, pix)
     sub = {k: (v[:, pix] if v.ndim == 2 else v[pix]) for k, v in got.items()}
-    rep = parity.compare(orc, sc, sub, ref, pix, rel_diverged=1e-9, h_ratio_only=True, h_ratio=10.0)
+    rep = parity.compare(orc, sc, sub, ref, pix, rel=5e-9, rel_diverged=5e-9, h_ratio_only=True, h_ratio=10.0)
     print("GBS kerr disk 1024^2 sampled:", rep)
 
 
