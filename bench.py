@@ -75,7 +75,7 @@ def parse():
     p.add_argument("--n", type=int, default=1024, help="camera resolution (default: the 1024^2 workload)")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="oracle sample budget per measurement")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--precision", default="fp64", choices=["fp64", "mixed", "mixed_pair"],
+    p.add_argument("--precision", default="fp64", choices=["fp64", "mixed", "mixed_pair", "double_float"],
                    help="path of the main measurement (default: the FP64 headline)")
     p.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision objects")
     p.add_argument("--method", default="dopri5", choices=list(METHODS),
@@ -95,11 +95,15 @@ def dist_env():
     return rank, world, local
 
 
-PRECISIONS = {"fp64": 0, "mixed": 1, "mixed_pair": 2}
+PRECISIONS = {"fp64": 0, "mixed": 1, "mixed_pair": 2, "double_float": 3}
 
 
 def workload(n, precision="fp64", method="dopri5"):
     from paper_2609_08989_gb300 import scenes
+    if precision == "double_float":
+        if method != "dopri5":
+            raise SystemExit("the double-float path steps with Dormand-Prince only")
+        return scenes.kerr_disk(n).replace(precision=PRECISIONS[precision])
     if precision == "fp64":
         sc = scenes.kerr_disk(n).replace(method=METHODS[method])
         if method == "verlet":
@@ -316,6 +320,20 @@ def run_tartarus(args):
 
     mixed = {}
     if not args.no_mixed and args.precision == "fp64":
+        # the double-float path on the headline image itself (same tolerance, FP64-class results)
+        dsc = workload(args.n, "double_float")
+        ms, dout = time_variant(T, dsc, max(2, args.steps // 2), 1, flush)
+        h = dout["h_max"].cpu().numpy()
+        esc = dout["code"].cpu().numpy() == 0
+        att = int(dout["steps"].sum().item() + dout["rejects"].sum().item())
+        eq = FLOPS_PER_STEP * att / (ms / 1e3) / 1e12
+        mixed["double_float"] = {
+            "value": dsc.npix / (ms / 1e3), "unit": UNIT, "ms_per_image": ms, "workload": dsc.name,
+            "rtol": dsc.rtol, "arithmetic": "every stage in FP32-pair (double-float, ~48-bit) on the FP32 pipe",
+            "h_max_escaped": float(h[esc].max()) if esc.any() else None,
+            "h_max_escaped_p99": float(np.percentile(h[esc], 99)) if esc.any() else None,
+            "rk_step_attempts_per_image": att,
+            "fp64_equivalent_tflops": eq, "fp64_equivalent_vs_fp64_peak": eq / FP64_PEAK_TFLOPS}
         # the mixed-precision paths on the same Kerr disk scene at 2048^2, each at
         # the tolerance that keeps |H| <= 1e-6 on escaped rays
         for name in ("mixed", "mixed_pair"):
@@ -380,7 +398,8 @@ def run_tartarus(args):
             "clocks": clk,
         }
         if args.precision != "fp64":
-            line["dtype"] = "f32 stages / f64 state" if args.precision == "mixed" else "f32 stages / f32-pair state"
+            line["dtype"] = {"mixed": "f32 stages / f64 state", "mixed_pair": "f32 stages / f32-pair state",
+                             "double_float": "f32 pair (double-float)"}[args.precision]
             line["roofline"] = None          # the FP64 flop count does not describe the mixed step
         if sc.method not in FLOPS_PER_STEP_METHOD:
             line["roofline"] = None          # Verlet: flops per step vary with its fixed-point iterations

@@ -69,6 +69,7 @@ extern "C" {
 #define TT_FP64          0   /* all arithmetic in binary64             */
 #define TT_MIXED         1   /* FP32 stages, FP64 state accumulation   */
 #define TT_MIXED_PAIR    2   /* FP32 stages, compensated FP32-pair state accumulation (~48 bits) */
+#define TT_DOUBLE_FLOAT  3   /* every stage in double-float (FP32 pairs, ~48 bits) on the FP32 pipe */
 #define TT_REFINE_HENON   0  /* exact step onto theta = pi/2 (default) */
 #define TT_REFINE_HERMITE 1  /* paper's cubic-Hermite bisection        */
 #define TT_REFINE_HENON64 2  /* Henon with FP64 stages on the mixed paths too (default there: FP32 stages) */
@@ -105,8 +106,13 @@ typedef struct {
  * r < fp64_radius_factor * r_h run in FP64 (0 selects 1.5, negative: none);
  * so do steps that start with sin(theta) < fp64_pole_sin (0 selects 0.1,
  * negative: none), where L^2 / sin^2(theta) makes FP32 lose the constraint.
- * TT_MIXED and TT_MIXED_PAIR are available for the closed-form Kerr metric;
- * with a table they return TT_EUNSUPPORTED.  On the mixed paths h_max is the
+ * TT_MIXED and TT_MIXED_PAIR run the steps near the horizon and the axis in
+ * double-float (FP32-pair, ~48-bit) arithmetic on the FP32 pipe.
+ * TT_DOUBLE_FLOAT steps every ray in double-float: flow, stage points, stage
+ * sums (with double-float coefficients) and the state, with an FP32 error
+ * estimate and step control; crossings are refined and emission evaluated in
+ * FP64.  TT_MIXED, TT_MIXED_PAIR and TT_DOUBLE_FLOAT are available for the
+ * closed-form Kerr metric; with a table they return TT_EUNSUPPORTED.  On the mixed paths h_max is the
  * largest |H| evaluated in FP64: at the start, at every FP64 step, at the
  * start of every step with a disk crossing, every monitor_period warp
  * iterations and at the end.
@@ -129,7 +135,7 @@ typedef struct {
  * TT_DP54 only. */
 typedef struct {
     int method;                 /* TT_DP54, TT_CK45, TT_F45, TT_GBS or TT_VERLET */
-    int precision;              /* TT_FP64, TT_MIXED or TT_MIXED_PAIR */
+    int precision;              /* TT_FP64, TT_MIXED, TT_MIXED_PAIR or TT_DOUBLE_FLOAT */
     double rtol, atol, h0, h_min;
     long long max_steps;
     double horizon_eps, escape_factor;

@@ -16,8 +16,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 SO = os.path.join(BUILD, "libtartarus.so")
 SOURCES = ["tt_capi.cu", "tt_kernel64.cu", "tt_kernel_mixed.cu", "tt_kernel_ck.cu", "tt_kernel_f.cu",
-           "tt_kernel_gbs.cu", "tt_kernel_verlet.cu"]
-HEADERS = ["tt_internal.h", "tt_device.cuh", "tt_trace.cuh", "tt_kernel_rk.cuh", os.path.join("..", "..", "include", "tartarus.h")]
+           "tt_kernel_gbs.cu", "tt_kernel_verlet.cu", "tt_kernel_df.cu"]
+HEADERS = ["tt_internal.h", "tt_device.cuh", "tt_df.cuh", "tt_trace.cuh", "tt_kernel_rk.cuh", os.path.join("..", "..", "include", "tartarus.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
 # The FP64 kernels write every fused multiply-add explicitly; without contraction

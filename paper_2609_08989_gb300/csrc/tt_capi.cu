@@ -57,7 +57,9 @@ int check_metric(const tt_metric* m) {
 int check_solver(const tt_solver* s) {
     if (!s) return TT_EINVAL;
     if (s->method < TT_DP54 || s->method > TT_VERLET) return TT_EINVAL;
-    if (s->precision != TT_FP64 && s->precision != TT_MIXED && s->precision != TT_MIXED_PAIR) return TT_EINVAL;
+    if (s->precision != TT_FP64 && s->precision != TT_MIXED && s->precision != TT_MIXED_PAIR &&
+        s->precision != TT_DOUBLE_FLOAT)
+        return TT_EINVAL;
     if (s->method != TT_DP54 && s->precision != TT_FP64) return TT_EUNSUPPORTED;
     if (!is_finite(s->rtol) || !is_finite(s->atol) || !(s->rtol > 0.0) || !(s->atol > 0.0)) return TT_EINVAL;
     if (!is_finite(s->h0) || !is_finite(s->h_min)) return TT_EINVAL;

@@ -157,7 +157,7 @@ struct StateF {
 };
 
 // M, a^2 and r_+ - r_- in FP32; dr = r - r_+.
-__device__ __forceinline__ void kerr_flow32(float M, float a2, float rpm, const RayConstF& R, const StateF& y,
+__device__ __forceinline__ void kerr_flow32_body(float M, float a2, float rpm, const RayConstF& R, const StateF& y,
                                             float dr, StateF& f, float& H) {
     float s, c;
     sincosf(y.th, &s, &c);
@@ -188,6 +188,28 @@ __device__ __forceinline__ void kerr_flow32(float M, float a2, float rpm, const 
     f.th = y.pth * iS;
     f.pr = -G * iD * hiS;
     f.pth = -fmaf(4.0f * a2 * sc, H, dKt) * hiS;
+}
+
+// The FP32 flow as one shared out-of-line copy (arguments and results by
+// value, so they travel in registers): the mixed kernels call it from many
+// stages, and inlining it everywhere made instruction-cache misses, not
+// arithmetic, their bound.
+struct Flow32 {
+    StateF f;
+    float H;
+};
+
+static __device__ __noinline__ Flow32 kerr_flow32_call(float M, float a2, float rpm, RayConstF R, StateF y, float dr) {
+    Flow32 o;
+    kerr_flow32_body(M, a2, rpm, R, y, dr, o.f, o.H);
+    return o;
+}
+
+__device__ __forceinline__ void kerr_flow32(float M, float a2, float rpm, const RayConstF& R, const StateF& y,
+                                            float dr, StateF& f, float& H) {
+    const Flow32 o = kerr_flow32_call(M, a2, rpm, R, y, dr);
+    f = o.f;
+    H = o.H;
 }
 
 // H alone (no derivatives), FP64: the mixed paths' constraint monitor.

@@ -28,6 +28,7 @@
 #include <cuda_runtime.h>
 
 #include "tt_device.cuh"
+#include "tt_df.cuh"
 #include "tt_internal.h"
 
 namespace tt {
@@ -54,7 +55,35 @@ __device__ __forceinline__ double step_factor(double err2) {
 // Dormand-Prince kn is the seventh stage (first same as last); for Cash-Karp
 // and Fehlberg it is evaluated after the six stages.
 // ---------------------------------------------------------------------------
-template <int METRIC, int METHOD = 0>
+// The FP64 closed-form flow as one out-of-line copy (arguments and results by
+// value), for kernels whose instruction footprint matters more than the call.
+struct Flow64 {
+    State f;
+    double H;
+};
+
+static __device__ __noinline__ Flow64 kerr_flow64_v(KerrK k, RayConst R, State y) {
+    Flow64 o;
+    kerr_flow64(k, R, y, o.f, o.H);
+    return o;
+}
+
+__device__ __forceinline__ void kerr_flow64_call(const KerrK& k, const RayConst& R, const State& y, State& f,
+                                                 double& H) {
+    const Flow64 o = kerr_flow64_v(k, R, y);
+    f = o.f;
+    H = o.H;
+}
+
+// CALL: evaluate the closed-form flow through kerr_flow64_call.
+template <int METRIC, bool CALL>
+__device__ __forceinline__ void flow64s(const ImageDesc& d, const KerrK& kk, const RayConst& R, const State& y,
+                                        State& f, double& H) {
+    if constexpr (CALL && METRIC == 0) kerr_flow64_call(kk, R, y, f, H);
+    else flow64<METRIC>(d, kk, R, y, f, H);
+}
+
+template <int METRIC, int METHOD = 0, bool CALL = false>
 __device__ __forceinline__ void rk_step64(const ImageDesc& d, const KerrK& kk, const RayConst& R,
                                            const State& y, const State& k1, double h, State& yn,
                                            State& kn, double& Hn, State& err) {
@@ -66,7 +95,7 @@ __device__ __forceinline__ void rk_step64(const ImageDesc& d, const KerrK& kk, c
     ys.th = fma(h, (expr_t), y.th);                                                  \
     ys.pr = fma(h, (expr_p), y.pr);                                                  \
     ys.pth = fma(h, (expr_q), y.pth);                                                \
-    flow64<METRIC>(d, kk, R, ys, dst, Hs);
+    flow64s<METRIC, CALL>(d, kk, R, ys, dst, Hs);
 // stages 2-4: coefficients pre-multiplied by h (one multiply each, shared by
 // the four components), the stage point an FMA chain from y
 #define TT_PSTAGE(dst, EXPR)                                                         \
@@ -74,7 +103,7 @@ __device__ __forceinline__ void rk_step64(const ImageDesc& d, const KerrK& kk, c
     ys.th = EXPR(th);                                                                \
     ys.pr = EXPR(pr);                                                                \
     ys.pth = EXPR(pth);                                                              \
-    flow64<METRIC>(d, kk, R, ys, dst, Hs);
+    flow64s<METRIC, CALL>(d, kk, R, ys, dst, Hs);
     const double h21 = h * T::a21, h31 = h * T::a31, h32 = h * T::a32;
     const double h41 = h * T::a41, h42 = h * T::a42, h43 = h * T::a43;
 #define TT_P2(f) fma(h21, k1.f, y.f)
@@ -92,7 +121,7 @@ __device__ __forceinline__ void rk_step64(const ImageDesc& d, const KerrK& kk, c
     yn.th = fma(h, TT_C7(th), y.th);
     yn.pr = fma(h, TT_C7(pr), y.pr);
     yn.pth = fma(h, TT_C7(pth), y.pth);
-    flow64<METRIC>(d, kk, R, yn, kn, Hn);
+    flow64s<METRIC, CALL>(d, kk, R, yn, kn, Hn);
 #define TT_E(f) \
     h * TT_MAC(T::e7, kn.f, fma(T::e6, k6.f, fma(T::e5, k5.f, fma(T::e4, k4.f, fma(T::e3, k3.f, T::e1 * k1.f)))))
     err.r = TT_E(r);
@@ -476,6 +505,13 @@ struct Lane {
     float thpf;             // FP64 steps within this angle of the axis
     float hf, lamf;         // step size and affine parameter of the FP32 steps
     bool k64_ok, k32_ok;
+    // double-float steps: low parts of the flow at the state (valid with k1f if
+    // kdf_ok), the spacetime and ray constants, and the running max of |H|
+    StateF k1lo;
+    bool kdf_ok;
+    float hmaxf;
+    KerrDF kdf;
+    RayDF rdf;
 };
 
 __device__ __forceinline__ void write_final(const Lane& L, int code) {
@@ -484,7 +520,7 @@ __device__ __forceinline__ void write_final(const Lane& L, int code) {
     d.code[q] = (int8_t)code;
     d.n_cross[q] = (int8_t)min(L.ncross, 127);
     d.intensity[q] = L.inten;
-    d.h_max[q] = L.hmax;
+    d.h_max[q] = fmax(L.hmax, (double)L.hmaxf);
     d.steps[q] = L.steps;
     d.rejects[q] = L.rejects;
     for (int k = L.nrec; k < kMaxCross; ++k) {
@@ -596,6 +632,8 @@ __device__ bool init_ray(Lane& L, const ImageDesc* d_ptr, long long q, const Sol
     L.y.pth = -p_th;
     L.R = make_ray_const(d.a, -p_t, -p_ph);
     L.k32_ok = false;
+    L.kdf_ok = false;
+    L.hmaxf = 0.0f;
     if (sol.precision == 0) {
         double H0;
         flow64<METRIC>(d, L.kk, L.R, L.y, L.k1, H0);
@@ -620,7 +658,19 @@ __device__ bool init_ray(Lane& L, const ImageDesc* d_ptr, long long q, const Sol
         float H0;
         kerr_flow32(L.Mf, L.a2f, L.rpmf, L.Rf, yf, dr0, L.k1f, H0);
         L.k32_ok = true;
-        L.hf = (sol.h0 > 0.0) ? (float)sol.h0 : initial_step32(L, yf, dr0, (float)sol.atol, (float)sol.rtol);
+        if (sol.precision == 3) {
+            // double-float path: the FP64 path's starting step (once per ray), so
+            // that both begin the same step sequence
+            L.kdf = make_kerr_df(L.kk);
+            L.rdf = make_ray_df(L.R);
+            double H64;
+            flow64<METRIC>(d, L.kk, L.R, L.y, L.k1, H64);
+            L.hmax = fabs(H64);
+            L.hf = (float)((sol.h0 > 0.0) ? sol.h0
+                                         : initial_step64<METRIC>(d, L.kk, L.R, L.y, L.k1, sol.atol, sol.rtol));
+        } else {
+            L.hf = (sol.h0 > 0.0) ? (float)sol.h0 : initial_step32(L, yf, dr0, (float)sol.atol, (float)sol.rtol);
+        }
         L.h = (double)L.hf;
     }
     return true;
@@ -742,7 +792,7 @@ template <int METRIC, int PREC, int METHOD = 0>
 __device__ void refine_pending(Lane& L, const SolverDesc& sol) {
     const ImageDesc& d = *L.d;
     double rc;
-    if (PREC != 0 && sol.refine != 2) {
+    if ((PREC == 1 || PREC == 2) && sol.refine != 2) {
         rc = refine_henon32(L, L.yc, d.r_plus, (float)sol.atol, (float)sol.rtol);
     } else {
         State f0;
@@ -782,7 +832,7 @@ __device__ int step_ray64(Lane& L, const SolverDesc& sol) {
     } else if constexpr (METHOD == 3) {
         gbs_step64<METRIC>(d, L.kk, L.R, L.y, L.k1, L.h, yn, kn, Hn, e);
     } else {
-        rk_step64<METRIC, METHOD>(d, L.kk, L.R, L.y, L.k1, L.h, yn, kn, Hn, e);
+        rk_step64<METRIC, METHOD, (PREC != 0)>(d, L.kk, L.R, L.y, L.k1, L.h, yn, kn, Hn, e);
     }
     // Verlet: fixed step, always accepted
     const double err2 = (METHOD == 4) ? 0.0 : err_norm2(L.y, yn, e, sol.atol, sol.rtol);
@@ -950,6 +1000,7 @@ __device__ int step_ray32(Lane& L, StateF& yhi, const SolverDesc& sol) {
         L.lamf += h;
         L.k1f = k7;
         L.k64_ok = false;
+        L.kdf_ok = false;
         if (captured) return 1;
         if (escaped) return 0;
         float fac = (err2 < 1e-30f) ? 10.0f : 0.9f * __powf(err2, -0.1f);
@@ -958,6 +1009,191 @@ __device__ int step_ray32(Lane& L, StateF& yhi, const SolverDesc& sol) {
         L.last_rej = false;
     } else {
         L.rejects++;
+        L.hf = h * fmaxf(0.2f, 0.9f * __powf(err2, -0.1f));
+        L.last_rej = true;
+    }
+    return -1;
+}
+
+// ---------------------------------------------------------------------------
+// One Dormand-Prince step in double-float (~48 bits) on the FP32 pipe: the
+// mixed paths' steps near the horizon and the axis (FULL false), and every step
+// of the double-float path (FULL true).  The flow is always evaluated in
+// double-float at stage points held in double-float, and the new state is
+// accumulated in double-float.  FULL forms the stage sums sum_j a_ij k_j in
+// double-float with double-float coefficients; otherwise the (small) stage
+// increments h sum_j a_ij k_j are formed in FP32 from the high parts and the
+// fifth-order sum uses FP32 coefficients -- a perturbation of ~6e-8 of a step's
+// change, far below the mixed paths' tolerance.  The error norm and the
+// step-size control run in FP32.  ACC 0: the state is the FP64 L.y;
+// ACC 1: the FP32 pair (yhi, L.lo).
+// ---------------------------------------------------------------------------
+template <int ACC, bool FULL>
+__device__ int step_ray_df(Lane& L, StateF& yhi, const SolverDesc& sol) {
+    constexpr int PREC = FULL ? 3 : ACC + 1;
+    const ImageDesc& d = *L.d;
+    if ((long long)L.steps + (long long)L.rejects >= sol.max_steps) return 2;
+    const float h = L.hf;
+    const float hmin = (sol.h_min > 0.0) ? (float)sol.h_min : 1e-14f * fmaxf(1.0f, L.lamf);
+    if (h < hmin) return 3;
+    using namespace dp;
+    KerrDF kd;
+    RayDF rd;
+    if constexpr (FULL) {
+        kd = L.kdf;
+        rd = L.rdf;
+    } else {
+        kd = make_kerr_df(L.kk);
+        rd = make_ray_df(L.R);
+    }
+    StateDF y;
+    if constexpr (ACC == 0) {
+        y = StateDF{df_of(L.y.r), df_of(L.y.th), df_of(L.y.pr), df_of(L.y.pth)};
+    } else {
+        y = StateDF{DF{yhi.r, L.lo.r}, DF{yhi.th, L.lo.th}, DF{yhi.pr, L.lo.pr}, DF{yhi.pth, L.lo.pth}};
+    }
+    DF Hs;
+    StateDF k1;
+    if (!L.kdf_ok) {
+        kerr_flow_df(kd, rd, y, k1, Hs);
+    } else {
+        k1 = StateDF{DF{L.k1f.r, L.k1lo.r}, DF{L.k1f.th, L.k1lo.th}, DF{L.k1f.pr, L.k1lo.pr},
+                     DF{L.k1f.pth, L.k1lo.pth}};
+    }
+    StateDF k2, k3, k4, k5, k6, k7, ys, yn;
+#define TT_DS(dst, S)                                                                 \
+    ys.r = S(r);                                                                      \
+    ys.th = S(th);                                                                    \
+    ys.pr = S(pr);                                                                    \
+    ys.pth = S(pth);                                                                  \
+    kerr_flow_df(kd, rd, ys, dst, Hs);
+    if constexpr (FULL) {
+        constexpr DF A21 = df_const(a21), A31 = df_const(a31), A32 = df_const(a32);
+        constexpr DF A41 = df_const(a41), A42 = df_const(a42), A43 = df_const(a43);
+        constexpr DF A51 = df_const(a51), A52 = df_const(a52), A53 = df_const(a53), A54 = df_const(a54);
+        constexpr DF A61 = df_const(a61), A62 = df_const(a62), A63 = df_const(a63), A64 = df_const(a64),
+                     A65 = df_const(a65);
+        constexpr DF B1 = df_const(b1), B3 = df_const(b3), B4 = df_const(b4), B5 = df_const(b5), B6 = df_const(b6);
+#define TT_F2(f) df_add(y.f, df_mul_f(df_mul(k1.f, A21), h))
+#define TT_F3(f) df_add(y.f, df_mul_f(df_fma(k2.f, A32, df_mul(k1.f, A31)), h))
+#define TT_F4(f) df_add(y.f, df_mul_f(df_fma(k3.f, A43, df_fma(k2.f, A42, df_mul(k1.f, A41))), h))
+#define TT_F5(f) \
+    df_add(y.f, df_mul_f(df_fma(k4.f, A54, df_fma(k3.f, A53, df_fma(k2.f, A52, df_mul(k1.f, A51)))), h))
+#define TT_F6(f)                                                                                         \
+    df_add(y.f, df_mul_f(df_fma(k5.f, A65, df_fma(k4.f, A64, df_fma(k3.f, A63, df_fma(k2.f, A62,        \
+                                                                                       df_mul(k1.f, A61))))), h))
+#define TT_F7(f)                                                                                         \
+    df_add(y.f, df_mul_f(df_fma(k6.f, B6, df_fma(k5.f, B5, df_fma(k4.f, B4, df_fma(k3.f, B3,            \
+                                                                                    df_mul(k1.f, B1))))), h))
+        TT_DS(k2, TT_F2)
+        TT_DS(k3, TT_F3)
+        TT_DS(k4, TT_F4)
+        TT_DS(k5, TT_F5)
+        TT_DS(k6, TT_F6)
+        yn = StateDF{TT_F7(r), TT_F7(th), TT_F7(pr), TT_F7(pth)};
+#undef TT_F2
+#undef TT_F3
+#undef TT_F4
+#undef TT_F5
+#undef TT_F6
+#undef TT_F7
+    } else {
+#define TT_G2(f) df_add_f(y.f, h * ((float)a21 * k1.f.hi))
+#define TT_G3(f) df_add_f(y.f, h * fmaf((float)a32, k2.f.hi, (float)a31 * k1.f.hi))
+#define TT_G4(f) df_add_f(y.f, h * fmaf((float)a43, k3.f.hi, fmaf((float)a42, k2.f.hi, (float)a41 * k1.f.hi)))
+#define TT_G5(f)                                                                                         \
+    df_add_f(y.f, h * fmaf((float)a54, k4.f.hi, fmaf((float)a53, k3.f.hi, fmaf((float)a52, k2.f.hi,       \
+                                                                             (float)a51 * k1.f.hi))))
+#define TT_G6(f)                                                                                         \
+    df_add_f(y.f, h * fmaf((float)a65, k5.f.hi, fmaf((float)a64, k4.f.hi, fmaf((float)a63, k3.f.hi,      \
+                                               fmaf((float)a62, k2.f.hi, (float)a61 * k1.f.hi)))))
+#define TT_G7(f)                                                                                         \
+    df_add(y.f, df_mul_f(df_add(df_mul_f(k6.f, (float)b6), df_add(df_mul_f(k5.f, (float)b5),             \
+           df_add(df_mul_f(k4.f, (float)b4), df_add(df_mul_f(k3.f, (float)b3), df_mul_f(k1.f, (float)b1))))), h))
+        TT_DS(k2, TT_G2)
+        TT_DS(k3, TT_G3)
+        TT_DS(k4, TT_G4)
+        TT_DS(k5, TT_G5)
+        TT_DS(k6, TT_G6)
+        yn = StateDF{TT_G7(r), TT_G7(th), TT_G7(pr), TT_G7(pth)};
+#undef TT_G2
+#undef TT_G3
+#undef TT_G4
+#undef TT_G5
+#undef TT_G6
+#undef TT_G7
+    }
+#undef TT_DS
+    DF Hn;
+    kerr_flow_df(kd, rd, yn, k7, Hn);
+    // The error estimate h sum_i e_i k_i is a small difference of nearly equal
+    // stage flows (sum_i e_i = 0): at tolerances near 1e-10 it is formed in
+    // double-float with double-float weights (FULL), else FP32 rounding noise in
+    // it, not the truncation error, would set the step size.
+#define TT_E32(f)                                                                                       \
+    h * fmaf((float)e7, k7.f.hi, fmaf((float)e6, k6.f.hi, fmaf((float)e5, k5.f.hi, fmaf((float)e4, k4.f.hi, \
+             fmaf((float)e3, k3.f.hi, (float)e1 * k1.f.hi)))))
+#define TT_EDF(f)                                                                                       \
+    (h * df_fma(k7.f, E7, df_fma(k6.f, E6, df_fma(k5.f, E5, df_fma(k4.f, E4, df_fma(k3.f, E3,             \
+                                                                                    df_mul(k1.f, E1)))))).hi)
+    float er, eth, epr, epth;
+    if constexpr (FULL) {
+        constexpr DF E1 = df_const(e1), E3 = df_const(e3), E4 = df_const(e4), E5 = df_const(e5),
+                     E6 = df_const(e6), E7 = df_const(e7);
+        er = TT_EDF(r);
+        eth = TT_EDF(th);
+        epr = TT_EDF(pr);
+        epth = TT_EDF(pth);
+    } else {
+        er = TT_E32(r);
+        eth = TT_E32(th);
+        epr = TT_E32(pr);
+        epth = TT_E32(pth);
+    }
+#undef TT_E32
+#undef TT_EDF
+    const float atol = (float)sol.atol, rtol = (float)sol.rtol;
+    float err2 = sq_ratio32(er, y.r.hi, yn.r.hi, atol, rtol);
+    err2 += sq_ratio32(eth, y.th.hi, yn.th.hi, atol, rtol);
+    err2 += sq_ratio32(epr, y.pr.hi, yn.pr.hi, atol, rtol);
+    err2 += sq_ratio32(epth, y.pth.hi, yn.pth.hi, atol, rtol);
+    err2 *= 0.25f;
+    if (isnan(err2) || !isfinite(yn.r.hi) || !isfinite(yn.th.hi) || !isfinite(yn.pr.hi) || !isfinite(yn.pth.hi))
+        return 4;
+    if (err2 <= 1.0f) {
+        L.steps++;
+        const float pi2h = 1.57079637f, pi2l = -4.37113883e-08f;      // pi/2 as an FP32 pair
+        const bool s0 = !pair_below(pi2h, pi2l, y.th.hi, y.th.lo);      // theta <= pi/2 before
+        const bool s1 = !pair_below(pi2h, pi2l, yn.th.hi, yn.th.lo);    // and after
+        if (d.disk && s0 != s1) {
+            const State yc = (ACC == 0) ? L.y : pair_to64(yhi, L.lo);
+            note_crossing<0, PREC>(L, yc, sol);
+        }
+        if constexpr (ACC == 0) {
+            L.y = State{df_to64(yn.r), df_to64(yn.th), df_to64(yn.pr), df_to64(yn.pth)};
+        } else {
+            yhi = StateF{yn.r.hi, yn.th.hi, yn.pr.hi, yn.pth.hi};
+            L.lo = StateF{yn.r.lo, yn.th.lo, yn.pr.lo, yn.pth.lo};
+        }
+        L.k1f = StateF{k7.r.hi, k7.th.hi, k7.pr.hi, k7.pth.hi};
+        L.k1lo = StateF{k7.r.lo, k7.th.lo, k7.pr.lo, k7.pth.lo};
+        L.kdf_ok = true;
+        L.k32_ok = true;
+        L.k64_ok = false;
+        L.lamf += h;
+        L.hmaxf = fmaxf(L.hmaxf, fabsf(Hn.hi));
+        if (pair_below(yn.r.hi, yn.r.lo, L.caph, L.capl)) return 1;
+        if (yn.r.hi > L.escf) return 0;
+        float fac = (err2 < 1e-30f) ? 10.0f : 0.9f * __powf(err2, -0.1f);
+        fac = fminf(L.last_rej ? 1.0f : 10.0f, fmaxf(0.2f, fac));
+        L.hf = h * fac;
+        L.last_rej = false;
+    } else {
+        L.rejects++;
+        L.kdf_ok = true;                        // k1 still belongs to the unchanged state
+        L.k32_ok = true;
+        L.k1f = StateF{k1.r.hi, k1.th.hi, k1.pr.hi, k1.pth.hi};
+        L.k1lo = StateF{k1.r.lo, k1.th.lo, k1.pr.lo, k1.pth.lo};
         L.hf = h * fmaxf(0.2f, 0.9f * __powf(err2, -0.1f));
         L.last_rej = true;
     }
@@ -991,8 +1227,12 @@ template <int METRIC, int PREC, int METHOD = 0>
 __device__ __forceinline__ void trace_loop(const ImageDesc* descs, int n_desc, long long total,
                                            const SolverDesc& sol, const TuneParams& tp,
                                            unsigned long long* queue) {
-    static_assert(PREC == 0 || METHOD == 0, "the mixed paths step with Dormand-Prince");
-    constexpr int ACC = (PREC == 2) ? 1 : 0;
+    static_assert(PREC == 0 || METHOD == 0, "the mixed and double-float paths step with Dormand-Prince");
+    constexpr int ACC = (PREC >= 2) ? 1 : 0;
+    if constexpr (PREC != 0) {
+        df_sincos_table(s_df_tab);
+        __syncthreads();
+    }
     const int lane = threadIdx.x & 31;
     Lane L;
     L.pend = false;
@@ -1008,7 +1248,7 @@ __device__ __forceinline__ void trace_loop(const ImageDesc* descs, int n_desc, l
             (!drained || __any_sync(kFull, st == kDone))) {
             if (st != kIdle && L.pend) refine_pending<METRIC, PREC, METHOD>(L, sol);
             if (st == kDone) {
-                if (PREC != 0) check_h64<ACC>(L, yhi);
+                if (PREC == 1 || PREC == 2) check_h64<ACC>(L, yhi);
                 write_final(L, L.code);
                 st = kIdle;
             }
@@ -1038,7 +1278,15 @@ __device__ __forceinline__ void trace_loop(const ImageDesc* descs, int n_desc, l
         }
         ++iter;
         // ---- step phases ---------------------------------------------------
-        if (PREC == 0) {
+        if (PREC == 3) {
+            if (st == kRun) {
+                const int code = step_ray_df<1, true>(L, yhi, sol);
+                if (code >= 0) {
+                    L.code = code;
+                    st = kDone;
+                }
+            }
+        } else if (PREC == 0) {
             if (st == kRun) {
                 const int code = step_ray64<METRIC, 0, METHOD>(L, sol);
                 if (code >= 0) {
@@ -1059,17 +1307,8 @@ __device__ __forceinline__ void trace_loop(const ImageDesc* descs, int n_desc, l
                 const bool run64 = (__popc(w64) >= tp.fp64_batch) || (w64 == running) || (wait64 >= tp.fp64_wait);
                 wait64 = run64 ? 0 : wait64 + 1;
                 if (run64 && want64) {
-                    if (ACC == 1) L.y = pair_to64(yhi, L.lo);
-                    if (!L.k64_ok) {
-                        double H;
-                        flow64<0>(*L.d, L.kk, L.R, L.y, L.k1, H);
-                        L.k64_ok = true;
-                    }
-                    L.k32_ok = false;
-                    L.h = (double)L.hf;
-                    const int code = step_ray64<0, PREC>(L, sol);
-                    L.hf = (float)L.h;
-                    if (ACC == 1) split_state(L.y, yhi, L.lo);
+                    // the extended-precision step, in double-float on the FP32 pipe
+                    const int code = step_ray_df<ACC, false>(L, yhi, sol);
                     if (code >= 0) {
                         L.code = code;
                         st = kDone;
@@ -1090,7 +1329,7 @@ __device__ __forceinline__ void trace_loop(const ImageDesc* descs, int n_desc, l
             if (st == kRun && L.pend) refine_pending<METRIC, PREC, METHOD>(L, sol);
         }
         // ---- FP64 |H| monitor (mixed) --------------------------------------
-        if (PREC != 0 && (iter % (unsigned)tp.monitor_period) == 0) {
+        if ((PREC == 1 || PREC == 2) && (iter % (unsigned)tp.monitor_period) == 0) {
             if (st == kRun) check_h64<ACC>(L, yhi);
         }
     }
@@ -1135,8 +1374,11 @@ void fill_params(LaunchParams<N>& p, const ImageDesc* descs, int n, long long to
     for (int i = 0; i < n; ++i) p.desc[i] = descs[i];
 }
 
-// Mixed-precision launches (tt_kernel_mixed.cu).
+// Mixed-precision launches (tt_kernel_mixed.cu) and double-float launches
+// (tt_kernel_df.cu).
 cudaError_t launch_mixed(const ImageDesc* descs, int n, long long total, const SolverDesc& sol,
                          const LaunchShape& shape, unsigned long long* queue, cudaStream_t stream);
+cudaError_t launch_df(const ImageDesc* descs, int n, long long total, const SolverDesc& sol,
+                      const LaunchShape& shape, unsigned long long* queue, cudaStream_t stream);
 
 }  // namespace tt

@@ -26,7 +26,7 @@ from typing import List, Optional
 
 import numpy as np
 
-FP64, MIXED, MIXED_PAIR = 0, 1, 2
+FP64, MIXED, MIXED_PAIR, DOUBLE_FLOAT = 0, 1, 2, 3
 REFINE_HENON, REFINE_HERMITE, REFINE_HENON64 = 0, 1, 2
 DOPRI5, CASH_KARP, FEHLBERG, GBS, VERLET = 0, 1, 2, 3, 4
 METRIC_KERR, METRIC_TABLE = 0, 1
@@ -227,7 +227,7 @@ def batch_uneven(n_images: int = 64, seed: int = 2609, precision: int = MIXED,
         sc = kerr_disk(n, precision).replace(
             name="batch_%02d" % k, a=a, theta_obs=deg(inc), alpha_min=-half, alpha_max=half,
             beta_min=-half, beta_max=half)
-        if precision != FP64:
+        if precision in (MIXED, MIXED_PAIR):
             sc = sc.replace(rtol=MIXED_RTOL, atol=MIXED_RTOL)
         out.append(sc)
     return out

@@ -93,7 +93,7 @@ def test_unsupported_and_null_arguments():
     sc = scenes.kerr_disk(16)
     L = T.lib()
     for method in (1, 2, 3, 4):         # every integrator but Dormand-Prince runs in FP64 only
-        for prec in (1, 2):
+        for prec in (1, 2, 3):
             m, o, cam, s, d, out = _args(sc, s__method=method, s__precision=prec)
             assert L.tartarus_trace(C.byref(m), C.byref(o), C.byref(cam), C.byref(s), C.byref(d),
                                     C.byref(out), None, None) == T.TT_EUNSUPPORTED
