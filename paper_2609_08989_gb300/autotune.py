@@ -144,10 +144,11 @@ if __name__ == "__main__":
     import sys
     sys.path.insert(0, os.path.dirname(HERE))
     from paper_2609_08989_gb300 import scenes
-    which = sys.argv[1:] or ["fp64", "mixed", "mixed_pair"]
+    which = sys.argv[1:] or ["fp64", "mixed", "mixed_pair", "double_float"]
     todo = {"fp64": lambda: scenes.kerr_disk(1024),
             "mixed": lambda: scenes.kerr_disk_mixed(2048),
-            "mixed_pair": lambda: scenes.kerr_disk_mixed(2048).replace(precision=scenes.MIXED_PAIR)}
+            "mixed_pair": lambda: scenes.kerr_disk_mixed(2048).replace(precision=scenes.MIXED_PAIR),
+            "double_float": lambda: scenes.kerr_disk(1024).replace(precision=scenes.DOUBLE_FLOAT)}
     for name in which:
         sc = todo[name]()
         best, ms = tune_scene(sc, log=lambda m: print("  " + m, flush=True))
