@@ -60,8 +60,8 @@ FLOPS_PER_STEP_F32 = 6 * 72 + 232 + 20 + 5
 FP32_PEAK_TFLOPS = SM_COUNT * SM_MAX_MHZ * 1e6 * 128 * 2 / 1e12
 BYTES_OUT_PER_PIXEL = 3 * 3 * 8 + 8 + 8 + 4 + 4 + 1 + 1
 # DRAM traffic of the FP64 tracer per ray: ncu's dram__bytes_read.sum + dram__bytes_write.sum of
-# the 256^2 capture (profiles/trace_kernel64_kerr_disk_1024.md) divided by its 65,536 rays
-TRAFFIC_BYTES_PER_RAY = 386560.0 / 65536.0
+# the 512^2 capture (profiles/trace_kernel64_kerr_disk_1024.md) divided by its 262,144 rays
+TRAFFIC_BYTES_PER_RAY = (388096.0 + 7168.0) / 262144.0
 # host-to-device input of one step: the image descriptor (sizeof(tt::ImageDesc)) and the queue reset
 DESC_BYTES = 384 + 8
 
@@ -386,7 +386,7 @@ def run_tartarus(args):
                          "frac": achieved / FP64_PEAK_TFLOPS,
                          "traffic": (TRAFFIC_BYTES_PER_RAY * sc.npix
                                      if args.precision == "fp64" and sc.method == 0 else None),
-                         "traffic_note": "bytes per launch, scaled from a 256^2 ncu capture by rays",
+                         "traffic_note": "bytes per launch, scaled from a 512^2 ncu capture by rays",
                          "kernel": ("trace_kernel64_b256<0,1>" if sc.method == 0
                                     else "trace_kernel_rk<%d,0,1,256>" % sc.method), "kernel_ms": mean_kern,
                          "peak_source": "FP64 pipe: 152 SMs x 2070 MHz x 2 DFMA/clk (derived)",
