@@ -58,6 +58,9 @@ METHOD_NAMES = {v: k for k, v in METHODS.items()}
 # its stages, norm and control as in the FP64 step before the h-scaling above).
 FLOPS_PER_STEP_F32 = 6 * 72 + 232 + 20 + 5
 FP32_PEAK_TFLOPS = SM_COUNT * SM_MAX_MHZ * 1e6 * 128 * 2 / 1e12
+# FP32 thread instructions (FFMA + FMUL + FADD) per double-float step attempt, measured by ncu
+# on the 512^2 image (profiles/trace_kernel_df_kerr_disk_1024.md)
+DF_FP32_INST_PER_STEP = 5380
 BYTES_OUT_PER_PIXEL = 3 * 3 * 8 + 8 + 8 + 4 + 4 + 1 + 1
 # DRAM traffic of the FP64 tracer per ray: ncu's dram__bytes_read.sum + dram__bytes_write.sum of
 # the 512^2 capture (profiles/trace_kernel64_kerr_disk_1024.md) divided by its 262,144 rays
@@ -333,7 +336,13 @@ def run_tartarus(args):
             "h_max_escaped": float(h[esc].max()) if esc.any() else None,
             "h_max_escaped_p99": float(np.percentile(h[esc], 99)) if esc.any() else None,
             "rk_step_attempts_per_image": att,
-            "fp64_equivalent_tflops": eq, "fp64_equivalent_vs_fp64_peak": eq / FP64_PEAK_TFLOPS}
+            "fp64_equivalent_tflops": eq, "fp64_equivalent_vs_fp64_peak": eq / FP64_PEAK_TFLOPS,
+            "fp32_pipe": {"instructions_per_step": DF_FP32_INST_PER_STEP,
+                          "achieved_ginst_per_s": DF_FP32_INST_PER_STEP * att / (ms / 1e3) / 1e9,
+                          "peak_ginst_per_s": FP32_PEAK_TFLOPS / 2 * 1e3,
+                          "frac": DF_FP32_INST_PER_STEP * att / (ms / 1e3) / (FP32_PEAK_TFLOPS / 2 * 1e12),
+                          "source": "FP32 thread instructions per step from the 512^2 ncu capture "
+                                    "(profiles/trace_kernel_df_kerr_disk_1024.md)"}}
         # the mixed-precision paths on the same Kerr disk scene at 2048^2, each at
         # the tolerance that keeps |H| <= 1e-6 on escaped rays
         for name in ("mixed", "mixed_pair"):
