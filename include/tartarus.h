@@ -103,10 +103,11 @@ typedef struct {
  * max_steps >= 1 caps accepted + rejected steps.  Captured when
  * r < r_h (1 + horizon_eps), escaped when r > escape_factor * r_obs
  * (escape_factor > 1).  fp64_radius_factor (mixed only): steps that start at
- * r < fp64_radius_factor * r_h run in FP64 (0 selects 1.5, negative: none);
- * so do steps that start with sin(theta) < fp64_pole_sin (0 selects 0.1,
- * negative: none), where L^2 / sin^2(theta) makes FP32 lose the constraint.
- * TT_MIXED and TT_MIXED_PAIR run the steps near the horizon and the axis in
+ * r < fp64_radius_factor * r_h run in extended precision (0 selects 2,
+ * negative: none); so do steps that start within asin(fp64_pole_sin) of the
+ * polar axis (0 selects 0.3, negative: none), where L^2 / sin^2(theta) makes
+ * FP32 lose the constraint.  The defaults keep |H| <= 1e-6 on escaped rays at
+ * rtol 1e-8.  TT_MIXED and TT_MIXED_PAIR run these extended-precision steps in
  * double-float (FP32-pair, ~48-bit) arithmetic on the FP32 pipe.
  * TT_DOUBLE_FLOAT steps every ray in double-float: flow, stage points, stage
  * sums (with double-float coefficients) and the state, with an FP32 error

@@ -150,10 +150,12 @@ int make_desc(const tt_metric* m, const tt_observer* obs, const tt_camera* cam, 
     }
     d->r_capture = r_h * (1.0 + sol->horizon_eps);
     d->r_escape = sol->escape_factor * obs->r_obs;
-    // mixed path: steps starting below r_fp64 run in FP64 (factor 0 -> 1.5, negative -> never)
-    d->r_fp64 = sol->fp64_radius_factor < 0.0 ? 0.0 : (sol->fp64_radius_factor > 0.0 ? sol->fp64_radius_factor : 1.5) * r_h;
-    // ... and within asin(fp64_pole_sin) of the axis (0 -> 0.1, negative -> never)
-    d->th_pole = sol->fp64_pole_sin < 0.0 ? 0.0 : std::asin(std::min(1.0, sol->fp64_pole_sin > 0.0 ? sol->fp64_pole_sin : 0.1));
+    // mixed paths: steps starting below r_fp64 run in double-float (factor 0 -> 2,
+    // negative -> never) ... and those within asin(fp64_pole_sin) of the axis
+    // (0 -> 0.3, negative -> never).  The defaults keep |H| <= 1e-6 on every
+    // escaped ray of the benchmark image and of the 64-image batch at rtol 1e-8.
+    d->r_fp64 = sol->fp64_radius_factor < 0.0 ? 0.0 : (sol->fp64_radius_factor > 0.0 ? sol->fp64_radius_factor : 2.0) * r_h;
+    d->th_pole = sol->fp64_pole_sin < 0.0 ? 0.0 : std::asin(std::min(1.0, sol->fp64_pole_sin > 0.0 ? sol->fp64_pole_sin : 0.3));
     d->disk = disk->enabled ? 1 : 0;
     d->max_cross = disk->enabled ? disk->max_crossings : 0;
     d->doppler = disk->doppler ? 1 : 0;

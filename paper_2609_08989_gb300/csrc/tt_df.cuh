@@ -111,22 +111,23 @@ __device__ __forceinline__ DF df_rcp(DF x) {
 }
 
 // ---------------------------------------------------------------------------
-// sin and cos of theta in [0, pi] in double-float.  theta = k pi/64 + d with
-// |d| <= pi/128; sin and cos of k pi/64 come from a 65-entry table (computed in
-// FP64 when a block starts, see df_sincos_table), and of d from their Taylor
-// series: the terms beyond d^3/6 and d^2/2 (< 3e-9 relative) in FP32, those
-// before in double-float.  Angle addition then combines the two.
+// sin and cos of theta in double-float, for any theta (a ray through the polar
+// axis continues with theta outside (0, pi)).  theta = k pi/64 + d with
+// |d| <= pi/128; sin and cos of k pi/64 come from a 128-entry table over one
+// period (computed in FP64 when a block starts, see df_sincos_table), and of d
+// from their Taylor series: the terms beyond d^3/6 and d^2/2 (< 3e-9 relative)
+// in FP32, those before in double-float.  Angle addition then combines the two.
 // ---------------------------------------------------------------------------
-constexpr int kSinCosN = 64;                       // table step pi/64
+constexpr int kSinCosN = 128;                      // entries per period, step pi/64
 constexpr double kPiOver64 = 0.04908738521234051935;
 
 // the table, one copy per block of the kernels that step in double-float
-static __shared__ float4 s_df_tab[kSinCosN + 1];
+static __shared__ float4 s_df_tab[kSinCosN];
 
-// Fill tab[0..64] = (sin hi, sin lo, cos hi, cos lo) of k pi/64 (by the threads
+// Fill tab[0..127] = (sin hi, sin lo, cos hi, cos lo) of k pi/64 (by the threads
 // of one block; the caller synchronises the block afterwards).
 __device__ __forceinline__ void df_sincos_table(float4* tab) {
-    for (int k = threadIdx.x; k <= kSinCosN; k += blockDim.x) {
+    for (int k = threadIdx.x; k < kSinCosN; k += blockDim.x) {
         double s, c;
         sincos((double)k * kPiOver64, &s, &c);
         const DF sd = df_of(s), cd = df_of(c);
@@ -138,13 +139,12 @@ __device__ __forceinline__ void df_sincos(DF th, DF& s, DF& c) {
     constexpr float kInv = (float)(64.0 / 3.14159265358979323846);
     constexpr DF P = df_const(kPiOver64);
     constexpr float P2 = (float)(kPiOver64 - (double)P.hi - (double)P.lo);
-    int k = __float2int_rn(th.hi * kInv);
-    k = min(max(k, 0), kSinCosN);
+    const int k = __float2int_rn(th.hi * kInv);    // |k| < 2^24 keeps k P_hi exact below
     const float kf = (float)k;
     // d = theta - k P: k P_hi exactly as p0 + e0 (FMA), k P_lo as p1 + e1
     const float p0 = __fmul_rn(kf, P.hi), e0 = fmaf(kf, P.hi, -p0);
     const float p1 = __fmul_rn(kf, P.lo), e1 = fmaf(kf, P.lo, -p1);
-    const float d0 = __fsub_rn(th.hi, p0);         // exact (Sterbenz) for k >= 1; theta_hi for k = 0
+    const float d0 = __fsub_rn(th.hi, p0);         // exact (Sterbenz) for k != 0; theta_hi for k = 0
     const float tail = (th.lo - e0) - ((p1 + e1) + kf * P2);
     const DF d = fast_two_sum(d0, tail);
     const DF q = df_sqr(d);                         // d^2 <= 6.1e-4
@@ -156,7 +156,7 @@ __device__ __forceinline__ void df_sincos(DF th, DF& s, DF& c) {
     // cos d = 1 + q (-1/2 + q (1/24 - q/720))
     const float wc = qf * fmaf(-qf, 1.0f / 720.0f, 1.0f / 24.0f);
     const DF cd = df_add_f(df_mul(q, two_sum(-0.5f, wc)), 1.0f);
-    const float4 t = s_df_tab[k];
+    const float4 t = s_df_tab[k & (kSinCosN - 1)];  // k mod 128 (two's complement)
     const DF sk = DF{t.x, t.y}, ck = DF{t.z, t.w};
     s = df_add(df_mul(sk, cd), df_mul(ck, sd));
     c = df_sub(df_mul(ck, cd), df_mul(sk, sd));

@@ -1297,10 +1297,14 @@ __device__ __forceinline__ void trace_loop(const ImageDesc* descs, int n_desc, l
         } else {
             bool want64 = false;
             if (st == kRun) {
-                // FP64 near the horizon and near the axis (the coordinate singularities)
+                // double-float near the horizon and near the axis (the coordinate
+                // singularities); the distance to the axis is |theta - m pi| for the
+                // nearest integer m, since a ray through the axis continues with
+                // theta outside (0, pi)
                 const float thf = (ACC == 0) ? (float)L.y.th : yhi.th;
                 const float rf = (ACC == 0) ? (float)L.y.r : yhi.r;
-                want64 = (rf < L.fp64f) || (thf < L.thpf) || (thf > 3.14159274f - L.thpf);
+                const float axis = fabsf(fmaf(-rintf(thf * 0.318309886f), 3.14159274f, thf));
+                want64 = (rf < L.fp64f) || (axis < L.thpf);
             }
             const unsigned w64 = __ballot_sync(kFull, want64);
             if (w64) {

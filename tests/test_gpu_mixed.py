@@ -6,8 +6,10 @@ Bars: termination codes equal outside the band around the critical curve
 crossing radii and g factors within 1e-5 relative on the primary crossing of
 every pixel outside that band (higher-order crossings orbit the photon region
 and amplify any difference exponentially, so they are reported, not gated);
-|H| <= 1e-6 on escaped rays (evaluated in FP64 by the kernel), gated at the
-99.9th percentile with the maximum reported.
+|H| <= 1e-6 on every escaped ray (evaluated in FP64 by the kernel) with the
+default extended-precision zones (within 2 r_+ of the hole and asin(0.3) of
+the axis), on the benchmark's 2048^2 image and on the 64-image batch; with the
+horizon zone switched off, at the 99.9th percentile.
 """
 import numpy as np
 import pytest
@@ -71,10 +73,11 @@ def test_mixed_against_oracle(T, orc, ref256, precision, fp64_factor, refine):
     over = np.nonzero(esc & (got["h_max"] > 1e-6))[0]
     if len(over):
         print("escaped rays above 1e-6:", [(int(q), float(got["h_max"][q])) for q in over[:10]])
-    # |H| <= 1e-6 on escaped rays: gated at the 99.9th percentile (a few rays that
-    # graze the edge of the FP64 polar zone reach ~2e-6; the maximum is reported)
-    assert np.percentile(got["h_max"][esc], 99.9) <= 1e-6
-    assert got["h_max"][esc].max() <= 5e-6
+    if fp64_factor == 0.0:
+        assert got["h_max"][esc].max() <= 1e-6
+    else:
+        assert np.percentile(got["h_max"][esc], 99.9) <= 1e-6
+        assert got["h_max"][esc].max() <= 5e-6
 
 
 def test_mixed_full_size_sampled(T, orc):
@@ -91,6 +94,25 @@ def test_mixed_full_size_sampled(T, orc):
     assert np.percentile(rel, 99) < 1e-5
     esc = sub["code"] == 0
     assert np.percentile(sub["h_max"][esc], 99.9) <= 1e-6
+    # every escaped ray of the whole image
+    assert got["h_max"][got["code"] == 0].max() <= 1e-6
+
+
+def test_mixed_batch_h_bound(T):
+    """The 64 uneven images (spins to 0.998, inclinations 5-85 deg, odd and even
+    grids, so zero-angular-momentum rays through the axis too) in one launch:
+    |H| <= 1e-6 on every escaped ray."""
+    imgs = scenes.batch_uneven(64, seed=2609, precision=scenes.MIXED_PAIR)
+    outs = T.trace_batch(imgs)
+    torch.cuda.synchronize()
+    worst = 0.0
+    for sc, o in zip(imgs, outs):
+        got = T.to_numpy(o)
+        assert set(np.unique(got["code"])) <= {0, 1}
+        esc = got["code"] == 0
+        worst = max(worst, float(got["h_max"][esc].max()))
+    print("batch escaped |H| max %.3e" % worst)
+    assert worst <= 1e-6
 
 
 def test_mixed_table_is_unsupported(T, orc):
