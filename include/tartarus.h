@@ -110,13 +110,15 @@ typedef struct {
  * rtol 1e-8.  TT_MIXED and TT_MIXED_PAIR run these extended-precision steps in
  * double-float (FP32-pair, ~48-bit) arithmetic on the FP32 pipe.
  * TT_DOUBLE_FLOAT steps every ray in double-float: flow, stage points, stage
- * sums (with double-float coefficients) and the state, with an FP32 error
- * estimate and step control; crossings are refined and emission evaluated in
- * FP64.  TT_MIXED, TT_MIXED_PAIR and TT_DOUBLE_FLOAT are available for the
- * closed-form Kerr metric; with a table they return TT_EUNSUPPORTED.  On the mixed paths h_max is the
- * largest |H| evaluated in FP64: at the start, at every FP64 step, at the
- * start of every step with a disk crossing, every monitor_period warp
- * iterations and at the end.
+ * sums and error estimate (with double-float coefficients) and the state, with
+ * an FP32 error norm and step control; crossings are refined and emission
+ * evaluated in FP64.  TT_MIXED, TT_MIXED_PAIR and TT_DOUBLE_FLOAT are available
+ * for the closed-form Kerr metric; with a table they return TT_EUNSUPPORTED.
+ * h_max is the largest |H| seen: on the FP64 path at the start and after every
+ * accepted step; on the double-float path at the start (FP64) and after every
+ * accepted step (double-float); on the mixed paths after every double-float
+ * step, and in FP64 at the start of every step with a disk crossing, every
+ * monitor_period warp iterations and at the end.
  * method: one of the five integrators of Sec. 3.2.  The embedded 5(4) pairs
  * (TT_DP54, TT_CK45, TT_F45) propagate their fifth-order solution and take the
  * difference to the fourth-order one as the error estimate.  TT_GBS: macro-
@@ -196,11 +198,11 @@ typedef struct {
  *   blocks_per_sm   persistent blocks per SM (0: as many as fit)
  *   crossing_batch  refine disk crossings once this many lanes of a warp have
  *                   one pending (1..32; default 8 FP64, 16 mixed)
- *   fp64_batch      mixed paths: run the FP64 near-horizon steps once this many
+ *   fp64_batch      mixed paths: run the extended-precision zone steps once this many
  *                   lanes need one (1..32, default 16)
  *   monitor_period  mixed paths: evaluate |H| in FP64 every this many warp
  *                   iterations (default 32)
- *   fp64_wait       mixed paths: lanes waiting for an FP64 step get one after at
+ *   fp64_wait       mixed paths: lanes waiting for a zone step get one after at
  *                   most this many warp iterations (default 64) */
 typedef struct {
     int block;

@@ -35,8 +35,8 @@ struct ImageDesc {
     // events
     double r_capture;             // r_h (1 + horizon_eps)
     double r_escape;              // escape_factor * r_obs
-    double r_fp64;                // mixed path: FP64 steps below this radius
-    double th_pole;               // mixed path: FP64 steps within this angle of the axis
+    double r_fp64;                // mixed paths: double-float steps below this radius
+    double th_pole;               // mixed paths: double-float steps within this angle of the axis
     double r_plus, r_minus;       // Kerr horizons (mixed path: Delta = (r - r_+)(r - r_-))
     // disk
     int disk, max_cross, doppler;
@@ -82,9 +82,9 @@ struct LaunchShape {
 struct TuneParams {
     int refill;           // refill when at least this many lanes are done or idle
     int crossing_batch;   // refine crossings once this many lanes have one pending
-    int fp64_batch;       // mixed: run FP64 steps once this many lanes need one
+    int fp64_batch;       // mixed: run the double-float zone steps once this many lanes need one
     int monitor_period;   // mixed: FP64 |H| check every this many iterations
-    int fp64_wait;        // mixed: FP64 steps run after this many iterations of waiting
+    int fp64_wait;        // mixed: zone steps run after this many iterations of waiting
 };
 
 // Images handed to one launch by value (kernel parameters, no host-to-device

@@ -2,22 +2,22 @@
 //
 // One ray per thread; warps pull rays from a shared queue (one atomicAdd per
 // warp refill).  On GB300 an FP64 instruction issues at 1/64 of the FP32 rate
-// and a warp pays for its inactive lanes, so per-ray FP64 work outside the
+// and a warp pays for its inactive lanes, so per-ray side work outside the
 // regular step (initial data, crossing refinement and emission, the final
-// record, the mixed path's FP64 steps and |H| checks) runs in warp-uniform
-// phases in which every lane that needs it takes part at once:
+// record, the mixed path's extended-precision steps and |H| checks) runs in
+// warp-uniform phases in which every lane that needs it takes part at once:
 //
 //   refill phase  : when >= `refill` lanes are done or idle (or none runs):
 //                   pending crossings are refined, finished rays are written,
 //                   idle lanes take new rays and build their initial data;
-//   FP64 steps    : FP64 path: every running lane.  Mixed path: lanes near the
-//                   horizon (r < r_fp64) or the axis (sin theta < the pole
-//                   threshold) wait until `fp64_batch` of them (or every
-//                   running lane) need an FP64 step, or they have waited
-//                   `fp64_wait` iterations;
-//   FP32 steps    : mixed path, every other running lane;
+//   steps         : FP64 and double-float paths: every running lane.  Mixed
+//                   paths: lanes near the horizon (r < r_fp64) or the axis
+//                   (within the pole angle) take a double-float step once
+//                   `fp64_batch` of them (or every running lane) need one, or
+//                   they have waited `fp64_wait` iterations; the others an
+//                   FP32 step;
 //   crossings     : once >= `crossing_batch` lanes have a crossing pending;
-//   |H| check     : mixed path, every `monitor_period` iterations, in FP64.
+//   |H| check     : mixed paths, every `monitor_period` iterations, in FP64.
 //
 // Every loop is bounded: a lane takes at most max_steps steps per ray and each
 // warp iteration either steps rays or consumes queue entries; nothing waits on
@@ -55,35 +55,7 @@ __device__ __forceinline__ double step_factor(double err2) {
 // Dormand-Prince kn is the seventh stage (first same as last); for Cash-Karp
 // and Fehlberg it is evaluated after the six stages.
 // ---------------------------------------------------------------------------
-// The FP64 closed-form flow as one out-of-line copy (arguments and results by
-// value), for kernels whose instruction footprint matters more than the call.
-struct Flow64 {
-    State f;
-    double H;
-};
-
-static __device__ __noinline__ Flow64 kerr_flow64_v(KerrK k, RayConst R, State y) {
-    Flow64 o;
-    kerr_flow64(k, R, y, o.f, o.H);
-    return o;
-}
-
-__device__ __forceinline__ void kerr_flow64_call(const KerrK& k, const RayConst& R, const State& y, State& f,
-                                                 double& H) {
-    const Flow64 o = kerr_flow64_v(k, R, y);
-    f = o.f;
-    H = o.H;
-}
-
-// CALL: evaluate the closed-form flow through kerr_flow64_call.
-template <int METRIC, bool CALL>
-__device__ __forceinline__ void flow64s(const ImageDesc& d, const KerrK& kk, const RayConst& R, const State& y,
-                                        State& f, double& H) {
-    if constexpr (CALL && METRIC == 0) kerr_flow64_call(kk, R, y, f, H);
-    else flow64<METRIC>(d, kk, R, y, f, H);
-}
-
-template <int METRIC, int METHOD = 0, bool CALL = false>
+template <int METRIC, int METHOD = 0>
 __device__ __forceinline__ void rk_step64(const ImageDesc& d, const KerrK& kk, const RayConst& R,
                                            const State& y, const State& k1, double h, State& yn,
                                            State& kn, double& Hn, State& err) {
@@ -95,7 +67,7 @@ __device__ __forceinline__ void rk_step64(const ImageDesc& d, const KerrK& kk, c
     ys.th = fma(h, (expr_t), y.th);                                                  \
     ys.pr = fma(h, (expr_p), y.pr);                                                  \
     ys.pth = fma(h, (expr_q), y.pth);                                                \
-    flow64s<METRIC, CALL>(d, kk, R, ys, dst, Hs);
+    flow64<METRIC>(d, kk, R, ys, dst, Hs);
 // stages 2-4: coefficients pre-multiplied by h (one multiply each, shared by
 // the four components), the stage point an FMA chain from y
 #define TT_PSTAGE(dst, EXPR)                                                         \
@@ -103,7 +75,7 @@ __device__ __forceinline__ void rk_step64(const ImageDesc& d, const KerrK& kk, c
     ys.th = EXPR(th);                                                                \
     ys.pr = EXPR(pr);                                                                \
     ys.pth = EXPR(pth);                                                              \
-    flow64s<METRIC, CALL>(d, kk, R, ys, dst, Hs);
+    flow64<METRIC>(d, kk, R, ys, dst, Hs);
     const double h21 = h * T::a21, h31 = h * T::a31, h32 = h * T::a32;
     const double h41 = h * T::a41, h42 = h * T::a42, h43 = h * T::a43;
 #define TT_P2(f) fma(h21, k1.f, y.f)
@@ -121,7 +93,7 @@ __device__ __forceinline__ void rk_step64(const ImageDesc& d, const KerrK& kk, c
     yn.th = fma(h, TT_C7(th), y.th);
     yn.pr = fma(h, TT_C7(pr), y.pr);
     yn.pth = fma(h, TT_C7(pth), y.pth);
-    flow64s<METRIC, CALL>(d, kk, R, yn, kn, Hn);
+    flow64<METRIC>(d, kk, R, yn, kn, Hn);
 #define TT_E(f) \
     h * TT_MAC(T::e7, kn.f, fma(T::e6, k6.f, fma(T::e5, k5.f, fma(T::e4, k4.f, fma(T::e3, k3.f, T::e1 * k1.f)))))
     err.r = TT_E(r);
@@ -501,8 +473,8 @@ struct Lane {
     float Mf, a2f, rpmf;    // M, a^2, r_+ - r_-
     float rph, rpl;         // r_+ as an FP32 pair
     float caph, capl;       // capture radius as an FP32 pair
-    float escf, fp64f;      // escape radius, FP64-step radius
-    float thpf;             // FP64 steps within this angle of the axis
+    float escf, fp64f;      // escape radius, extended-precision-step radius
+    float thpf;             // extended-precision steps within this angle of the axis
     float hf, lamf;         // step size and affine parameter of the FP32 steps
     bool k64_ok, k32_ok;
     // double-float steps: low parts of the flow at the state (valid with k1f if
@@ -832,7 +804,7 @@ __device__ int step_ray64(Lane& L, const SolverDesc& sol) {
     } else if constexpr (METHOD == 3) {
         gbs_step64<METRIC>(d, L.kk, L.R, L.y, L.k1, L.h, yn, kn, Hn, e);
     } else {
-        rk_step64<METRIC, METHOD, (PREC != 0)>(d, L.kk, L.R, L.y, L.k1, L.h, yn, kn, Hn, e);
+        rk_step64<METRIC, METHOD>(d, L.kk, L.R, L.y, L.k1, L.h, yn, kn, Hn, e);
     }
     // Verlet: fixed step, always accepted
     const double err2 = (METHOD == 4) ? 0.0 : err_norm2(L.y, yn, e, sol.atol, sol.rtol);
