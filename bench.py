@@ -58,6 +58,9 @@ METHOD_NAMES = {v: k for k, v in METHODS.items()}
 # its stages, norm and control as in the FP64 step before the h-scaling above).
 FLOPS_PER_STEP_F32 = 6 * 72 + 232 + 20 + 5
 FP32_PEAK_TFLOPS = SM_COUNT * SM_MAX_MHZ * 1e6 * 128 * 2 / 1e12
+# FP64 thread instructions per Dormand-Prince step attempt of the FP64 kernel, measured by ncu on
+# the 512^2 image (profiles/trace_kernel64_kerr_disk_1024.md): DFMA, DMUL, DADD
+FP64_ISSUED_PER_STEP = (323.0, 197.0, 13.5)
 # FP32 thread instructions (FFMA + FMUL + FADD) per double-float step attempt, measured by ncu
 # on the 512^2 image (profiles/trace_kernel_df_kerr_disk_1024.md)
 DF_FP32_INST_PER_STEP = 5380
@@ -400,7 +403,14 @@ def run_tartarus(args):
                                     else "trace_kernel_rk<%d,0,1,256>" % sc.method), "kernel_ms": mean_kern,
                          "peak_source": "FP64 pipe: 152 SMs x 2070 MHz x 2 DFMA/clk (derived)",
                          "flops_per_unit": fpu,
-                         "unit_of_work": "%s step attempt" % METHOD_NAMES[sc.method]},
+                         "unit_of_work": "%s step attempt" % METHOD_NAMES[sc.method],
+                         "issued": ({"fp64_flops_per_unit": 2 * FP64_ISSUED_PER_STEP[0] + sum(FP64_ISSUED_PER_STEP[1:]),
+                                     "tflops": (2 * FP64_ISSUED_PER_STEP[0] + sum(FP64_ISSUED_PER_STEP[1:]))
+                                               * step_attempts / (mean_kern / 1e3) / 1e12,
+                                     "frac": (2 * FP64_ISSUED_PER_STEP[0] + sum(FP64_ISSUED_PER_STEP[1:]))
+                                             * step_attempts / (mean_kern / 1e3) / 1e12 / FP64_PEAK_TFLOPS,
+                                     "source": "DFMA x 2 + DMUL + DADD per step from the 512^2 ncu capture"}
+                                    if sc.method == 0 else None)},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": DESC_BYTES,
                     "d2h_bytes_per_step": BYTES_OUT_PER_PIXEL * sc.npix},
             "gpu_launches": launches,
