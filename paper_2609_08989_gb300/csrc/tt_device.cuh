@@ -339,12 +339,30 @@ __device__ __forceinline__ void table_lower64(const ImageDesc& d, double r, doub
     g[4] = F[3];
 }
 
+// The table flow as one out-of-line copy (descriptor by pointer, the rest by
+// value): six stage evaluations and the refinement's inlined copies made the
+// table kernels' instruction footprint, not their FP64 arithmetic, a bound.
+struct FlowT64 {
+    State f;
+    double H;
+};
+
+static __device__ __noinline__ FlowT64 table_flow64_call(const ImageDesc* d, RayConst R, State y) {
+    FlowT64 o;
+    table_flow64(*d, R, y, o.f, o.H);
+    return o;
+}
+
 // METRIC: 0 closed-form Kerr, 1 table, 2 chosen per image at run time.
 template <int METRIC>
 __device__ __forceinline__ void flow64(const ImageDesc& d, const KerrK& k, const RayConst& R,
                                        const State& y, State& f, double& H) {
     if (METRIC == 0 || (METRIC == 2 && d.kind == 0)) kerr_flow64(k, R, y, f, H);
-    else table_flow64(d, R, y, f, H);
+    else {
+        const FlowT64 o = table_flow64_call(&d, R, y);
+        f = o.f;
+        H = o.H;
+    }
 }
 
 template <int METRIC>
