@@ -180,3 +180,23 @@ def test_step_cap_and_underflow_codes(orc):
     assert r["code"] == 5
     r = orc.trace_ray(sc, float("nan"), 0.0, cap=2)
     assert r["code"] == 5
+
+
+def test_photon_sphere_limit(orc):
+    """Schwarzschild rays just outside the critical impact parameter 3 sqrt(3) M
+    turn at the largest root of r^3 - b^2 r + 2 b^2 = 0, which tends to the
+    photon sphere r = 3M as b -> 3 sqrt(3) M; just inside, they are captured."""
+    D = 1000.0
+    sc = scenes.Scene(a=0.0, r_obs=D, theta_obs=math.pi / 2, rtol=1e-12, atol=1e-12)
+    bc = 3 * math.sqrt(3)
+    for eps in (1e-3, 1e-5):
+        b = bc * (1 + eps)
+        ray = orc.trace_ray(sc, b * math.sqrt(1 - 2.0 / D), 0.0, cap=200000)
+        assert ray["code"] == 0
+        roots = np.roots([1.0, 0.0, -b * b, 2 * b * b])
+        r_t = max(z.real for z in roots if abs(z.imag) < 1e-9)
+        r_min = ray["y"][:, 1].min()
+        assert 3.0 < r_t < 3.0 + 4 * math.sqrt(eps)
+        assert r_t * (1 - 1e-10) <= r_min < r_t * (1 + 2e-3)
+        inside = orc.trace_ray(sc, bc * (1 - eps) * math.sqrt(1 - 2.0 / D), 0.0, cap=2)
+        assert inside["code"] == 1
