@@ -55,19 +55,35 @@ __device__ __forceinline__ double step_factor(double err2) {
 // Dormand-Prince kn is the seventh stage (first same as last); for Cash-Karp
 // and Fehlberg it is evaluated after the six stages.
 // ---------------------------------------------------------------------------
+// On the closed-form metric (METRIC 0) the stages take sin and cos of theta
+// from (s0, c0) of the step start by angle addition, and the new point's are
+// returned in (sn, cn) for the next step (first same as last).
+template <int METRIC>
+__device__ __forceinline__ void flow64_near(const ImageDesc& d, const KerrK& kk, const RayConst& R, const State& y,
+                                            double th0, double s0, double c0, State& f, double& H, double& s,
+                                            double& c) {
+    if constexpr (METRIC == 0) {
+        sincos_near(y.th, th0, s0, c0, s, c);
+        kerr_flow64_sc(kk, R, y, s, c, f, H);
+    } else {
+        flow64<METRIC>(d, kk, R, y, f, H);
+    }
+}
+
 template <int METRIC, int METHOD = 0>
 __device__ __forceinline__ void rk_step64(const ImageDesc& d, const KerrK& kk, const RayConst& R,
                                            const State& y, const State& k1, double h, State& yn,
-                                           State& kn, double& Hn, State& err) {
+                                           State& kn, double& Hn, State& err, double s0 = 0.0, double c0 = 1.0,
+                                           double* sn = nullptr, double* cn = nullptr) {
     using T = RK<METHOD>;
     State k2, k3, k4, k5, k6, ys;
-    double Hs;
+    double Hs, ss = s0, cs = c0;
 #define TT_STAGE(dst, expr_r, expr_t, expr_p, expr_q)                                \
     ys.r = fma(h, (expr_r), y.r);                                                    \
     ys.th = fma(h, (expr_t), y.th);                                                  \
     ys.pr = fma(h, (expr_p), y.pr);                                                  \
     ys.pth = fma(h, (expr_q), y.pth);                                                \
-    flow64<METRIC>(d, kk, R, ys, dst, Hs);
+    flow64_near<METRIC>(d, kk, R, ys, y.th, s0, c0, dst, Hs, ss, cs);
 // stages 2-4: coefficients pre-multiplied by h (one multiply each, shared by
 // the four components), the stage point an FMA chain from y
 #define TT_PSTAGE(dst, EXPR)                                                         \
@@ -75,7 +91,7 @@ __device__ __forceinline__ void rk_step64(const ImageDesc& d, const KerrK& kk, c
     ys.th = EXPR(th);                                                                \
     ys.pr = EXPR(pr);                                                                \
     ys.pth = EXPR(pth);                                                              \
-    flow64<METRIC>(d, kk, R, ys, dst, Hs);
+    flow64_near<METRIC>(d, kk, R, ys, y.th, s0, c0, dst, Hs, ss, cs);
     const double h21 = h * T::a21, h31 = h * T::a31, h32 = h * T::a32;
     const double h41 = h * T::a41, h42 = h * T::a42, h43 = h * T::a43;
 #define TT_P2(f) fma(h21, k1.f, y.f)
@@ -93,7 +109,11 @@ __device__ __forceinline__ void rk_step64(const ImageDesc& d, const KerrK& kk, c
     yn.th = fma(h, TT_C7(th), y.th);
     yn.pr = fma(h, TT_C7(pr), y.pr);
     yn.pth = fma(h, TT_C7(pth), y.pth);
-    flow64<METRIC>(d, kk, R, yn, kn, Hn);
+    flow64_near<METRIC>(d, kk, R, yn, y.th, s0, c0, kn, Hn, ss, cs);
+    if (sn) {
+        *sn = ss;
+        *cn = cs;
+    }
 #define TT_E(f) \
     h * TT_MAC(T::e7, kn.f, fma(T::e6, k6.f, fma(T::e5, k5.f, fma(T::e4, k4.f, fma(T::e3, k3.f, T::e1 * k1.f)))))
     err.r = TT_E(r);
@@ -458,6 +478,7 @@ struct Lane {
     const ImageDesc* d;
     long long q;            // output index within the image
     State y, k1;            // FP64 state and its flow (first-same-as-last, valid if k64_ok)
+    double s0, c0;          // sin and cos of y.th (FP64 path, closed-form metric)
     RayConst R;
     KerrK kk;
     double h, lam, hmax, inten;
@@ -609,6 +630,7 @@ __device__ bool init_ray(Lane& L, const ImageDesc* d_ptr, long long q, const Sol
     if (sol.precision == 0) {
         double H0;
         flow64<METRIC>(d, L.kk, L.R, L.y, L.k1, H0);
+        sincos(L.y.th, &L.s0, &L.c0);
         L.hmax = fabs(H0);
         L.h = (sol.h0 > 0.0) ? sol.h0 : initial_step64<METRIC>(d, L.kk, L.R, L.y, L.k1, sol.atol, sol.rtol);
         L.k64_ok = true;
@@ -798,13 +820,13 @@ __device__ int step_ray64(Lane& L, const SolverDesc& sol) {
     const double hmin = (sol.h_min > 0.0) ? sol.h_min : 1e-14 * fmax(1.0, fabs(L.lam));
     if (L.h < hmin) return 3;
     State yn, kn, e;
-    double Hn;
+    double Hn, sn = L.s0, cn = L.c0;
     if constexpr (METHOD == 4) {
         verlet_step64<METRIC>(d, L.kk, L.R, L.y, L.k1, L.h, yn, kn, Hn);
     } else if constexpr (METHOD == 3) {
         gbs_step64<METRIC>(d, L.kk, L.R, L.y, L.k1, L.h, yn, kn, Hn, e);
     } else {
-        rk_step64<METRIC, METHOD>(d, L.kk, L.R, L.y, L.k1, L.h, yn, kn, Hn, e);
+        rk_step64<METRIC, METHOD>(d, L.kk, L.R, L.y, L.k1, L.h, yn, kn, Hn, e, L.s0, L.c0, &sn, &cn);
     }
     // Verlet: fixed step, always accepted
     const double err2 = (METHOD == 4) ? 0.0 : err_norm2(L.y, yn, e, sol.atol, sol.rtol);
@@ -825,6 +847,8 @@ __device__ int step_ray64(Lane& L, const SolverDesc& sol) {
         L.lam += L.h;
         L.y = yn;
         L.k1 = kn;
+        L.s0 = sn;
+        L.c0 = cn;
         L.hmax = fmax(L.hmax, fabs(Hn));
         if (yn.r < d.r_capture) return 1;
         if (yn.r > d.r_escape) return 0;
