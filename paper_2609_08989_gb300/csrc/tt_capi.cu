@@ -1,8 +1,9 @@
 // tt_capi.cu -- host side of the C ABI declared in include/tartarus.h.
 //
 // Validates the caller's structs, resolves per-image constants (event radii,
-// ISCO, Page-Thorne roots), uploads the image descriptors and a zeroed work
-// queue with stream-ordered allocations, and enqueues the persistent kernel.
+// ISCO, Page-Thorne roots, the observer's tetrad), zeroes a work-queue counter
+// from a per-device ring on the caller's stream and enqueues the persistent
+// kernel with the image descriptors as kernel parameters.
 #include <algorithm>
 #include <atomic>
 #include <mutex>

@@ -95,9 +95,45 @@ __device__ __forceinline__ DF df_sqr(DF x) {
     return fast_two_sum(p, e);
 }
 
-// x * y + z
+// x * y + z, the product's error term carried straight into the sum (no
+// intermediate renormalisation)
 __device__ __forceinline__ DF df_fma(DF x, DF y, DF z) {
-    return df_add(df_mul(x, y), z);
+    const float p = __fmul_rn(x.hi, y.hi);
+    float e = fmaf(x.hi, y.hi, -p);
+    e = fmaf(x.hi, y.lo, e);
+    e = fmaf(x.lo, y.hi, e);
+    const DF s = two_sum(p, z.hi);
+    return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(e, z.lo)));
+}
+
+// Dot products sum_j c_j k_j of double-float terms, in the style of Ogita,
+// Rump & Oishi's Dot2: the high parts' products are accumulated exactly with
+// TwoSum, and their rounding errors, the products' own errors (by FMA) and the
+// cross terms hi*lo are summed in FP32 -- as accurate as chained double-float
+// multiply-adds at ~3/4 of their instructions.
+struct DotAcc {
+    float s, t;
+};
+
+__device__ __forceinline__ float dot_err(DF c, DF k, float p) {
+    return fmaf(c.hi, k.hi, -p) + fmaf(c.hi, k.lo, c.lo * k.hi);
+}
+
+__device__ __forceinline__ DotAcc dot_first(DF c, DF k) {
+    const float p = __fmul_rn(c.hi, k.hi);
+    return DotAcc{p, dot_err(c, k, p)};
+}
+
+__device__ __forceinline__ DotAcc dot_next(DotAcc d, DF c, DF k) {
+    const float p = __fmul_rn(c.hi, k.hi);
+    const DF s = two_sum(d.s, p);
+    return DotAcc{s.hi, d.t + (s.lo + dot_err(c, k, p))};
+}
+
+// the final sum may be cancelled below the error terms: TwoSum, not FastTwoSum
+__device__ __forceinline__ DF dot_end(DotAcc d) {
+    const DF s = two_sum(d.s, d.t);
+    return fast_two_sum(s.hi, s.lo);
 }
 
 // 1/x: the correctly rounded FP32 reciprocal r0 leaves the residual

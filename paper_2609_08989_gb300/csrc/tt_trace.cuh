@@ -1071,16 +1071,18 @@ __device__ int step_ray_df(Lane& L, StateF& yhi, const SolverDesc& sol) {
                      A65 = df_const(a65);
         constexpr DF B1 = df_const(b1), B3 = df_const(b3), B4 = df_const(b4), B5 = df_const(b5), B6 = df_const(b6);
 #define TT_F2(f) df_add(y.f, df_mul_f(df_mul(k1.f, A21), h))
-#define TT_F3(f) df_add(y.f, df_mul_f(df_fma(k2.f, A32, df_mul(k1.f, A31)), h))
-#define TT_F4(f) df_add(y.f, df_mul_f(df_fma(k3.f, A43, df_fma(k2.f, A42, df_mul(k1.f, A41))), h))
-#define TT_F5(f) \
-    df_add(y.f, df_mul_f(df_fma(k4.f, A54, df_fma(k3.f, A53, df_fma(k2.f, A52, df_mul(k1.f, A51)))), h))
+#define TT_F3(f) df_add(y.f, df_mul_f(dot_end(dot_next(dot_first(A31, k1.f), A32, k2.f)), h))
+#define TT_F4(f) \
+    df_add(y.f, df_mul_f(dot_end(dot_next(dot_next(dot_first(A41, k1.f), A42, k2.f), A43, k3.f)), h))
+#define TT_F5(f)                                                                                         \
+    df_add(y.f, df_mul_f(dot_end(dot_next(dot_next(dot_next(dot_first(A51, k1.f), A52, k2.f), A53, k3.f), \
+                                          A54, k4.f)), h))
 #define TT_F6(f)                                                                                         \
-    df_add(y.f, df_mul_f(df_fma(k5.f, A65, df_fma(k4.f, A64, df_fma(k3.f, A63, df_fma(k2.f, A62,        \
-                                                                                       df_mul(k1.f, A61))))), h))
+    df_add(y.f, df_mul_f(dot_end(dot_next(dot_next(dot_next(dot_next(dot_first(A61, k1.f), A62, k2.f),   \
+                                                            A63, k3.f), A64, k4.f), A65, k5.f)), h))
 #define TT_F7(f)                                                                                         \
-    df_add(y.f, df_mul_f(df_fma(k6.f, B6, df_fma(k5.f, B5, df_fma(k4.f, B4, df_fma(k3.f, B3,            \
-                                                                                    df_mul(k1.f, B1))))), h))
+    df_add(y.f, df_mul_f(dot_end(dot_next(dot_next(dot_next(dot_next(dot_first(B1, k1.f), B3, k3.f),     \
+                                                            B4, k4.f), B5, k5.f), B6, k6.f)), h))
         TT_DS(k2, TT_F2)
         TT_DS(k3, TT_F3)
         TT_DS(k4, TT_F4)
@@ -1130,8 +1132,8 @@ __device__ int step_ray_df(Lane& L, StateF& yhi, const SolverDesc& sol) {
     h * fmaf((float)e7, k7.f.hi, fmaf((float)e6, k6.f.hi, fmaf((float)e5, k5.f.hi, fmaf((float)e4, k4.f.hi, \
              fmaf((float)e3, k3.f.hi, (float)e1 * k1.f.hi)))))
 #define TT_EDF(f)                                                                                       \
-    (h * df_fma(k7.f, E7, df_fma(k6.f, E6, df_fma(k5.f, E5, df_fma(k4.f, E4, df_fma(k3.f, E3,             \
-                                                                                    df_mul(k1.f, E1)))))).hi)
+    (h * dot_end(dot_next(dot_next(dot_next(dot_next(dot_next(dot_first(E1, k1.f), E3, k3.f), E4, k4.f),   \
+                                            E5, k5.f), E6, k6.f), E7, k7.f)).hi)
     float er, eth, epr, epth;
     if constexpr (FULL) {
         constexpr DF E1 = df_const(e1), E3 = df_const(e3), E4 = df_const(e4), E5 = df_const(e5),
