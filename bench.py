@@ -33,7 +33,8 @@ SM_MAX_MHZ = 2070.0
 FP64_PEAK_TFLOPS = SM_COUNT * SM_MAX_MHZ * 1e6 * 2 * 2 / 1e12
 # Algorithmic FP64 flops of one Dormand-Prince step attempt on the Kerr FP64 path,
 # counted from the kernel source of this build (FMA = 2; add, mul, reciprocal and
-# sqrt 1 each, the reciprocal's Newton refinement not counted; sin and cos 1 each):
+# sqrt 1 each, the reciprocal's Newton refinement not counted; sin and cos 1 each,
+# however they are evaluated -- here by angle addition from the step start):
 # 6 flow evaluations x 56 + stage combinations 226 (stages 2-4 with h-scaled
 # coefficients) + error norm 30 (one shared reciprocal) + step control 5.
 FLOW_FLOPS, NORM_FLOPS, CONTROL_FLOPS = 56, 30, 5
@@ -60,10 +61,10 @@ FLOPS_PER_STEP_F32 = 6 * 72 + 232 + 20 + 5
 FP32_PEAK_TFLOPS = SM_COUNT * SM_MAX_MHZ * 1e6 * 128 * 2 / 1e12
 # FP64 thread instructions per Dormand-Prince step attempt of the FP64 kernel, measured by ncu on
 # the 512^2 image (profiles/trace_kernel64_kerr_disk_1024.md): DFMA, DMUL, DADD
-FP64_ISSUED_PER_STEP = (323.0, 197.0, 13.5)
+FP64_ISSUED_PER_STEP = (281.2, 208.6, 19.5)
 # FP32 thread instructions (FFMA + FMUL + FADD) per double-float step attempt, measured by ncu
 # on the 512^2 image (profiles/trace_kernel_df_kerr_disk_1024.md)
-DF_FP32_INST_PER_STEP = 5380
+DF_FP32_INST_PER_STEP = 5030
 BYTES_OUT_PER_PIXEL = 3 * 3 * 8 + 8 + 8 + 4 + 4 + 1 + 1
 # DRAM traffic of the FP64 tracer per ray: ncu's dram__bytes_read.sum + dram__bytes_write.sum of
 # the 512^2 capture (profiles/trace_kernel64_kerr_disk_1024.md) divided by its 262,144 rays
