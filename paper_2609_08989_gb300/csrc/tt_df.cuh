@@ -137,13 +137,13 @@ __device__ __forceinline__ DF dot_end(DotAcc d) {
 }
 
 // 1/x: the correctly rounded FP32 reciprocal r0 leaves the residual
-// 1 - x_hi r0 exactly representable (one FMA), and one Newton correction
-// r0 (1 - x r0) restores ~48 bits.
+// e = 1 - x_hi r0 exactly representable (one FMA); 1/x = r0 (1 + e + e^2 + ...),
+// and the terms through e^2 (the last ~2^-48) restore double-float precision.
 __device__ __forceinline__ DF df_rcp(DF x) {
     const float r0 = __frcp_rn(x.hi);
     float e = fmaf(-x.hi, r0, 1.0f);
     e = fmaf(-x.lo, r0, e);
-    return fast_two_sum(r0, __fmul_rn(r0, e));
+    return fast_two_sum(r0, __fmul_rn(r0, fmaf(e, e, e)));
 }
 
 // ---------------------------------------------------------------------------
