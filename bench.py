@@ -465,6 +465,9 @@ def run_workload(args):
         direct = lambda: T.trace_batch(imgs, outs)
     elif args.workload == "table":
         sc = scenes.table_kerr_with_nodes(args.n if args.n != 1024 else 4096)
+        if args.precision not in ("fp64", "double_float"):
+            raise SystemExit("tabulated metrics are traced in FP64 or double-float")
+        sc = sc.replace(precision=PRECISIONS[args.precision])
         table = T.Table(sc.table, sc.r_min, sc.r_max)
         out = T.alloc_outputs(sc.npix)
         rays = sc.npix
@@ -472,9 +475,9 @@ def run_workload(args):
         launches_per_step = 1
         outs = [out]
         name = sc.name
-        dtype = "f64"
+        dtype = "f64" if args.precision == "fp64" else "f32 pair (double-float)"
         cfg = {"workload": name, "nx": sc.nx, "ny": sc.ny, "a": sc.a, "table": [512, 256], "rtol": sc.rtol,
-               "precision": "fp64"}
+               "precision": args.precision}
         direct = None
     else:
         # the paper's own scenes: Fig. 3 (e3), Table 1 (e5), the OSIRIS shadow of Figs. 5-6

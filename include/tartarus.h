@@ -102,18 +102,22 @@ typedef struct {
  * (Hairer-Norsett-Wanner starting-step algorithm).  h_min <= 0: 1e-14 max(1, |lambda|).
  * max_steps >= 1 caps accepted + rejected steps.  Captured when
  * r < r_h (1 + horizon_eps), escaped when r > escape_factor * r_obs
- * (escape_factor > 1).  fp64_radius_factor (mixed only): steps that start at
- * r < fp64_radius_factor * r_h run in extended precision (0 selects 2,
- * negative: none); so do steps that start within asin(fp64_pole_sin) of the
- * polar axis (0 selects 0.3, negative: none), where L^2 / sin^2(theta) makes
- * FP32 lose the constraint.  The defaults keep |H| <= 1e-6 on escaped rays at
- * rtol 1e-8.  TT_MIXED and TT_MIXED_PAIR run these extended-precision steps in
- * double-float (FP32-pair, ~48-bit) arithmetic on the FP32 pipe.
+ * (escape_factor > 1).  fp64_radius_factor (mixed paths, and the
+ * double-float path on a table): steps that start at r < fp64_radius_factor *
+ * r_h run in extended precision (0 selects 2, negative: none); so do steps that
+ * start within asin(fp64_pole_sin) of the polar axis (0 selects 0.3 on the
+ * mixed paths and none on a table, negative: none), where L^2 / sin^2(theta)
+ * makes FP32 lose the constraint.  The defaults keep |H| <= 1e-6 on escaped
+ * rays at rtol 1e-8.  TT_MIXED and TT_MIXED_PAIR run these extended-precision
+ * steps in double-float (FP32-pair, ~48-bit) arithmetic on the FP32 pipe.
  * TT_DOUBLE_FLOAT steps every ray in double-float: flow, stage points, stage
  * sums and error estimate (with double-float coefficients) and the state, with
  * an FP32 error norm and step control; crossings are refined and emission
- * evaluated in FP64.  TT_MIXED, TT_MIXED_PAIR and TT_DOUBLE_FLOAT are available
- * for the closed-form Kerr metric; with a table they return TT_EUNSUPPORTED.
+ * evaluated in FP64.  On a table its zone steps run in FP64, where the
+ * interpolated D = g_tt g_phiphi - g_tphi^2 goes to zero at the horizon.
+ * TT_MIXED and TT_MIXED_PAIR are available for the closed-form Kerr metric
+ * (with a table they return TT_EUNSUPPORTED); TT_DOUBLE_FLOAT for either
+ * kind, but a batch that mixes both kinds returns TT_EUNSUPPORTED for it.
  * h_max is the largest |H| seen: on the FP64 path at the start and after every
  * accepted step; on the double-float path at the start (FP64) and after every
  * accepted step (double-float); on the mixed paths after every double-float

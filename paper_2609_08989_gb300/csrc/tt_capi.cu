@@ -19,6 +19,7 @@
 
 struct tt_table {
     double* d_nodes;     // device nodes, local-slope form
+    float2* d_nodes_df;  // the same nodes as double-float pairs (hi, lo)
     int nr, nth;
     double r_min, r_max;
     int device;
@@ -31,6 +32,12 @@ std::atomic<long long> g_launches{0};
 bool is_finite(double x) { return std::isfinite(x); }
 
 double kerr_rplus(double M, double a) { return M + std::sqrt(M * M - a * a); }
+
+// the nearest double-float: hi = the float nearest v, lo = the float nearest v - hi
+float2 split_df(double v) {
+    const float hi = (float)v;
+    return make_float2(hi, (float)(v - (double)hi));
+}
 
 // Prograde ISCO, Bardeen, Press & Teukolsky (1972), a >= 0.
 double kerr_isco(double M, double a) {
@@ -119,15 +126,20 @@ int make_desc(const tt_metric* m, const tt_observer* obs, const tt_camera* cam, 
     d->M = m->M;
     d->a = m->a;
     double r_h;
-    if (m->kind == TT_METRIC_TABLE && sol->precision != TT_FP64) return TT_EUNSUPPORTED;
+    if (m->kind == TT_METRIC_TABLE && sol->precision != TT_FP64 && sol->precision != TT_DOUBLE_FLOAT)
+        return TT_EUNSUPPORTED;
     if (m->kind == TT_METRIC_TABLE) {
         const tt_table* t = m->table;
         d->table = t->d_nodes;
+        d->table_df = t->d_nodes_df;
         d->nr = t->nr;
         d->nth = t->nth;
         d->u0 = std::log(t->r_min);
         d->du = (std::log(t->r_max) - d->u0) / (double)(t->nr - 1);
         d->dth = M_PI / (double)(t->nth - 1);
+        d->u0_df = split_df(d->u0);
+        d->idu_df = split_df(1.0 / d->du);
+        d->idth_df = split_df(1.0 / d->dth);
         r_h = t->r_min;
     } else {
         r_h = kerr_rplus(m->M, m->a);
@@ -155,8 +167,13 @@ int make_desc(const tt_metric* m, const tt_observer* obs, const tt_camera* cam, 
     // negative -> never) ... and those within asin(fp64_pole_sin) of the axis
     // (0 -> 0.3, negative -> never).  The defaults keep |H| <= 1e-6 on every
     // escaped ray of the benchmark image and of the 64-image batch at rtol 1e-8.
+    // Double-float path on a table: the same zones run in FP64 (pole default:
+    // none -- the measured crossings and |H| do not change with it).
+    const bool df_table = m->kind == TT_METRIC_TABLE && sol->precision == TT_DOUBLE_FLOAT;
+    const double pole_default = df_table ? -1.0 : 0.3;
+    const double pole_sin = sol->fp64_pole_sin != 0.0 ? sol->fp64_pole_sin : pole_default;
     d->r_fp64 = sol->fp64_radius_factor < 0.0 ? 0.0 : (sol->fp64_radius_factor > 0.0 ? sol->fp64_radius_factor : 2.0) * r_h;
-    d->th_pole = sol->fp64_pole_sin < 0.0 ? 0.0 : std::asin(std::min(1.0, sol->fp64_pole_sin > 0.0 ? sol->fp64_pole_sin : 0.3));
+    d->th_pole = pole_sin < 0.0 ? 0.0 : std::asin(std::min(1.0, pole_sin));
     d->disk = disk->enabled ? 1 : 0;
     d->max_cross = disk->enabled ? disk->max_crossings : 0;
     d->doppler = disk->doppler ? 1 : 0;
@@ -245,11 +262,11 @@ int check_shape(const tt_tune* t) {
     return TT_OK;
 }
 
-// The kernels of the integrators other than Dormand-Prince take one metric
-// kind per launch: a batch with both closed-form Kerr and tabulated images is
-// refused for them.
+// The kernels of the integrators other than Dormand-Prince, and the
+// double-float kernels, take one metric kind per launch: a batch with both
+// closed-form Kerr and tabulated images is refused for them.
 int check_kinds(const tt_image* images, int n, const tt_solver* s) {
-    if (s->method == TT_DP54) return TT_OK;
+    if (s->method == TT_DP54 && s->precision != TT_DOUBLE_FLOAT) return TT_OK;
     bool kerr = false, table = false;
     for (int i = 0; i < n; ++i) {
         if (images[i].metric.kind == TT_METRIC_TABLE) table = true;
@@ -545,15 +562,24 @@ int tartarus_table_create(const double* host_nodes, int nr, int nth, double r_mi
             }
         }
     }
+    // the double-float copy
+    std::vector<float2> ldf(n);
+    for (size_t i = 0; i < n; ++i) ldf[i] = split_df(loc[i]);
     tt_table* t = new (std::nothrow) tt_table;
     if (!t) return TT_ENOMEM;
+    t->d_nodes = nullptr;
+    t->d_nodes_df = nullptr;
     cudaGetDevice(&t->device);
-    if (cudaMalloc((void**)&t->d_nodes, n * sizeof(double)) != cudaSuccess) {
+    if (cudaMalloc((void**)&t->d_nodes, n * sizeof(double)) != cudaSuccess ||
+        cudaMalloc((void**)&t->d_nodes_df, n * sizeof(float2)) != cudaSuccess) {
+        cudaFree(t->d_nodes);
         delete t;
         return TT_ENOMEM;
     }
-    if (cudaMemcpy(t->d_nodes, loc.data(), n * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) {
+    if (cudaMemcpy(t->d_nodes, loc.data(), n * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(t->d_nodes_df, ldf.data(), n * sizeof(float2), cudaMemcpyHostToDevice) != cudaSuccess) {
         cudaFree(t->d_nodes);
+        cudaFree(t->d_nodes_df);
         delete t;
         return TT_ECUDA;
     }
@@ -568,8 +594,9 @@ int tartarus_table_create(const double* host_nodes, int nr, int nth, double r_mi
 int tartarus_table_destroy(tt_table* t) {
     if (!t) return TT_EINVAL;
     cudaError_t e = cudaFree(t->d_nodes);
+    const cudaError_t e2 = cudaFree(t->d_nodes_df);
     delete t;
-    return e == cudaSuccess ? TT_OK : TT_ECUDA;
+    return (e == cudaSuccess && e2 == cudaSuccess) ? TT_OK : TT_ECUDA;
 }
 
 const char* tartarus_error_string(int status) {

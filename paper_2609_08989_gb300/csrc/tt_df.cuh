@@ -208,6 +208,7 @@ struct KerrDF {
 
 struct RayDF {
     DF pt, apph, pph2, a2pt2, c0, pt2;
+    DF ptsq, ptp;           // p_t^2, 2 p_t p_phi (tabulated metric)
 };
 
 __device__ __forceinline__ KerrDF make_kerr_df(const KerrK& k) {
@@ -215,7 +216,8 @@ __device__ __forceinline__ KerrDF make_kerr_df(const KerrK& k) {
 }
 
 __device__ __forceinline__ RayDF make_ray_df(const RayConst& R) {
-    return RayDF{df_of(R.pt), df_of(R.apph), df_of(R.pph2), df_of(R.a2pt2), df_of(R.c0), df_of(R.pt2)};
+    return RayDF{df_of(R.pt),    df_of(R.apph), df_of(R.pph2), df_of(R.a2pt2),
+                 df_of(R.c0),    df_of(R.pt2),  df_of(R.pt * R.pt), df_of(2.0 * R.pt * R.pph)};
 }
 
 __device__ __forceinline__ void kerr_flow_df_body(const KerrDF& k, const RayDF& R, const StateDF& y, StateDF& f,
@@ -268,6 +270,201 @@ __device__ __forceinline__ void kerr_flow_df(const KerrDF& k, const RayDF& R, co
     const FlowDF o = kerr_flow_df_call(k, R, y);
     f = o.f;
     H = o.H;
+}
+
+// ---------------------------------------------------------------------------
+// Natural logarithm in double-float, table-driven in the manner of Tang (ACM
+// TOMS 16, 1990): x = 2^e m with m in [1, 2) and c = 1 + k/32 the nearest
+// table point, ln x = e ln 2 + ln c + 2 atanh s with s = (m - c)/(m + c),
+// |s| <= 1/128.  The series 2 atanh s = 2 s + s^3 (2/3 + 2 s^2/5 + ...) keeps
+// s and s^3 2/3 in double-float and the rest (< 1.2e-11) in FP32; its first
+// omitted term is below 1e-24.  ln c comes from a 33-entry table computed in
+// FP64 when a block starts.
+// ---------------------------------------------------------------------------
+constexpr int kLnN = 32;
+
+// the table, one copy per block of the tabulated-metric double-float kernels
+static __shared__ float2 s_df_ln[kLnN + 1];
+
+// Fill tab[0..32] = ln(1 + k/32) (by the threads of one block; the caller
+// synchronises the block afterwards).
+__device__ __forceinline__ void df_log_table(float2* tab) {
+    for (int k = threadIdx.x; k <= kLnN; k += blockDim.x) {
+        const DF v = df_of(log1p((double)k / kLnN));
+        tab[k] = make_float2(v.hi, v.lo);
+    }
+}
+
+// ln x for x.hi positive and normal.
+__device__ __forceinline__ DF df_log(DF x) {
+    const int bits = __float_as_int(x.hi);
+    const int e = ((bits >> 23) & 0xff) - 127;
+    const float m = __int_as_float((bits & 0x007fffff) | 0x3f800000);      // in [1, 2)
+    const float ml = __fmul_rn(x.lo, __int_as_float((127 - e) << 23));     // x.lo 2^-e, exact
+    const int k = __float2int_rn(__fmul_rn(__fsub_rn(m, 1.0f), (float)kLnN));
+    const float c = fmaf((float)k, 1.0f / kLnN, 1.0f);                     // exact
+    // m - c is exact (Sterbenz) and a multiple of 2^-23, so at least |ml| or zero
+    const DF num = fast_two_sum(__fsub_rn(m, c), ml);
+    const DF den = df_add_f(DF{m, ml}, c);
+    const DF sv = df_mul(num, df_rcp(den));
+    const DF s2 = df_sqr(sv);
+    const float q = s2.hi;
+    const float w = q * fmaf(q, fmaf(q, 2.0f / 9.0f, 2.0f / 7.0f), 2.0f / 5.0f);
+    constexpr DF TWO3 = df_const(2.0 / 3.0);
+    const DF lm = df_add(DF{2.0f * sv.hi, 2.0f * sv.lo}, df_mul(df_mul(s2, sv), df_add_f(TWO3, w)));
+    // e ln 2 with ln 2 in three parts (the third keeps e ln 2 exact to ~2^-70 e)
+    constexpr double kLn2 = 0.69314718055994530942;
+    constexpr DF L2 = df_const(kLn2);
+    constexpr float L3 = (float)(kLn2 - (double)L2.hi - (double)L2.lo);
+    const float ef = (float)e;
+    DF el = df_mul_f(L2, ef);
+    el = df_add_f(el, ef * L3);
+    const float2 lc = s_df_ln[k];
+    return df_add(df_add(el, DF{lc.x, lc.y}), lm);
+}
+
+// ---------------------------------------------------------------------------
+// Tabulated metric in double-float: the bicubic Hermite patches of
+// table_fields64 (u = ln r, theta; nodes in local-slope form), each value and
+// slope an accumulation of 16 node terms in the Dot2 style above, with the
+// basis products computed once per node and shared by the five fields.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void hermite4_df(DF t, DF h[4], DF dh[4]) {
+    const DF t2 = df_sqr(t);
+    const DF omt = df_add_f(df_neg(t), 1.0f);                 // 1 - t
+    const DF omt2 = df_sqr(omt);
+    const DF tt = DF{2.0f * t.hi, 2.0f * t.lo};               // 2 t
+    h[0] = df_mul(df_add_f(tt, 1.0f), omt2);                  // (1 + 2t)(1 - t)^2
+    h[1] = df_mul(t, omt2);                                   // t (1 - t)^2
+    h[2] = df_mul(t2, df_add_f(df_neg(tt), 3.0f));            // t^2 (3 - 2t)
+    h[3] = df_neg(df_mul(t2, omt));                           // t^2 (t - 1)
+    dh[0] = df_mul_f(df_sub(t2, t), 6.0f);                    // 6 (t^2 - t)
+    dh[1] = df_mul(omt, df_add_f(df_mul_f(t, -3.0f), 1.0f));  // (1 - t)(1 - 3t)
+    dh[2] = df_neg(dh[0]);
+    dh[3] = df_mul(t, df_add_f(df_mul_f(t, 3.0f), -2.0f));    // t (3t - 2)
+}
+
+// Per-thread running sums of the table interpolation (15 per thread, strided by
+// the block size so that a warp's accesses fall in distinct banks); the
+// double-float kernels run 256-thread blocks.
+constexpr int kDfBlock = 256;
+constexpr int kDfAcc = 15;
+static __shared__ float2 s_df_acc[kDfAcc * kDfBlock];
+
+// floor(x) clamped to [0, n_max] (NaN to 0), for a double-float x
+__device__ __forceinline__ int df_cell(DF x, int n_max) {
+    float f = floorf(x.hi);
+    if (x.hi == f && x.lo < 0.0f) f -= 1.0f;
+    return (int)fminf(fmaxf(f, 0.0f), (float)n_max);
+}
+
+// All five fields (g_tt, g_tphi, g_thth, g_phiphi, g^rr) with d/dr and d/dth.
+__device__ __forceinline__ void table_fields_df(const ImageDesc& d, DF r, DF th, DF f[5], DF fr[5], DF ft[5]) {
+    const DF u0 = DF{d.u0_df.x, d.u0_df.y}, idu = DF{d.idu_df.x, d.idu_df.y};
+    const DF idth = DF{d.idth_df.x, d.idth_df.y};
+    const DF tu = df_mul(df_sub(df_log(r), u0), idu);
+    const DF tw = df_mul(th, idth);
+    const int k = df_cell(tu, d.nr - 2), j = df_cell(tw, d.nth - 2);
+    DF A[4], dA[4], B[4], dB[4];
+    hermite4_df(df_add_f(tu, -(float)k), A, dA);
+    hermite4_df(df_add_f(tw, -(float)j), B, dB);
+    const float2* n00 = d.table_df + ((size_t)j * d.nr + k) * kTableNF;
+    // the 15 running sums live in this thread's slots of s_df_acc, so that both
+    // loops below stay rolled: the flow is evaluated at every stage, and its
+    // unrolled form overflowed the instruction cache
+    float2* acc = s_df_acc + threadIdx.x;
+#pragma unroll
+    for (int q = 0; q < kDfAcc; ++q) acc[q * kDfBlock] = make_float2(0.0f, 0.0f);
+#pragma unroll 1
+    for (int nd = 0; nd < 4; ++nd) {
+        // node order (k, j), (k+1, j), (k, j+1), (k+1, j+1)
+        const bool cu = nd & 1, ct = nd >> 1;
+        const float2* node = n00 + (ct ? (size_t)d.nr * kTableNF : 0) + (cu ? kTableNF : 0);
+        const DF a0 = cu ? A[2] : A[0], a1 = cu ? A[3] : A[1], da0 = cu ? dA[2] : dA[0], da1 = cu ? dA[3] : dA[1];
+        const DF b0 = ct ? B[2] : B[0], b1 = ct ? B[3] : B[1], db0 = ct ? dB[2] : dB[0], db1 = ct ? dB[3] : dB[1];
+        // weights of the node's (F, F_u du, F_th dth, F_uth du dth) in the value,
+        // the u-slope and the theta-slope
+        const DF w0 = df_mul(a0, b0), w1 = df_mul(a1, b0), w2 = df_mul(a0, b1), w3 = df_mul(a1, b1);
+        const DF x0 = df_mul(da0, b0), x1 = df_mul(da1, b0), x2 = df_mul(da0, b1), x3 = df_mul(da1, b1);
+        const DF z0 = df_mul(a0, db0), z1 = df_mul(a1, db0), z2 = df_mul(a0, db1), z3 = df_mul(a1, db1);
+#pragma unroll 1
+        for (int fi = 0; fi < 5; ++fi) {
+            const float4* p = reinterpret_cast<const float4*>(node + 4 * fi);
+            const float4 q0 = __ldg(p), q1 = __ldg(p + 1);    // (F, F_u), (F_th, F_uth)
+            const DF F = DF{q0.x, q0.y}, Fu = DF{q0.z, q0.w}, Ft = DF{q1.x, q1.y}, Fut = DF{q1.z, q1.w};
+            float2* a = acc + 3 * fi * kDfBlock;
+            const float2 v0 = a[0], v1 = a[kDfBlock], v2 = a[2 * kDfBlock];
+            const DotAcc v = dot_next(dot_next(dot_next(dot_next(DotAcc{v0.x, v0.y}, w0, F), w1, Fu), w2, Ft), w3, Fut);
+            const DotAcc vu = dot_next(dot_next(dot_next(dot_next(DotAcc{v1.x, v1.y}, x0, F), x1, Fu), x2, Ft), x3, Fut);
+            const DotAcc vt = dot_next(dot_next(dot_next(dot_next(DotAcc{v2.x, v2.y}, z0, F), z1, Fu), z2, Ft), z3, Fut);
+            a[0] = make_float2(v.s, v.t);
+            a[kDfBlock] = make_float2(vu.s, vu.t);
+            a[2 * kDfBlock] = make_float2(vt.s, vt.t);
+        }
+    }
+    const DF inv_dur = df_mul(idu, df_rcp(r));                 // 1 / (du r)
+#pragma unroll
+    for (int fi = 0; fi < 5; ++fi) {
+        const float2 v0 = acc[3 * fi * kDfBlock], v1 = acc[(3 * fi + 1) * kDfBlock], v2 = acc[(3 * fi + 2) * kDfBlock];
+        f[fi] = dot_end(DotAcc{v0.x, v0.y});
+        fr[fi] = df_mul(dot_end(DotAcc{v1.x, v1.y}), inv_dur);
+        ft[fi] = df_mul(dot_end(DotAcc{v2.x, v2.y}), idth);
+    }
+}
+
+// The flow of table_flow64 in double-float: H = 1/2 [W/D + g^rr p_r^2 +
+// p_th^2 / g_thth] with D = g_tt g_phiphi - g_tphi^2 and
+// W = g_phiphi p_t^2 - 2 g_tphi p_t p_phi + g_tt p_phi^2.
+__device__ __forceinline__ void table_flow_df(const ImageDesc& d, const RayDF& R, const StateDF& y, StateDF& f,
+                                              DF& H) {
+    DF F[5], Fr[5], Ft[5];
+    table_fields_df(d, y.r, y.th, F, Fr, Ft);
+    const DF D = df_sub(df_mul(F[0], F[3]), df_sqr(F[1]));
+    const DF iD = df_rcp(D);
+    const DF W = dot_end(dot_next(dot_next(dot_first(F[3], R.ptsq), df_neg(F[1]), R.ptp), F[0], R.pph2));
+    const DF WiD = df_mul(W, iD);
+    const DF ith = df_rcp(F[2]);
+    const DF pr2 = df_sqr(y.pr);
+    const DF pthi = df_mul(y.pth, ith);                      // p_th / g_thth
+    const DF pth2i = df_mul(y.pth, pthi);
+    const DF H2 = df_add(WiD, df_fma(F[4], pr2, pth2i));
+    H = DF{0.5f * H2.hi, 0.5f * H2.lo};
+    const DF pthi2 = df_sqr(pthi);                           // p_th^2 / g_thth^2
+    // d(2H)/dx = (dW - W/D dD)/D + d(g^rr) p_r^2 - d(g_thth) p_th^2 / g_thth^2
+#define TT_D2H(G)                                                                                            \
+    df_add(df_mul(df_sub(dot_end(dot_next(dot_next(dot_first(G[3], R.ptsq), df_neg(G[1]), R.ptp), G[0], R.pph2)), \
+                         df_mul(WiD, dot_end(dot_next(dot_next(dot_first(G[0], F[3]), F[0], G[3]),                \
+                                                      DF{-2.0f * F[1].hi, -2.0f * F[1].lo}, G[1])))),           \
+                  iD),                                                                                         \
+           df_sub(df_mul(G[4], pr2), df_mul(G[2], pthi2)))
+    const DF d2H_r = TT_D2H(Fr);
+    const DF d2H_t = TT_D2H(Ft);
+#undef TT_D2H
+    f.r = df_mul(F[4], y.pr);
+    f.th = pthi;
+    f.pr = DF{-0.5f * d2H_r.hi, -0.5f * d2H_r.lo};
+    f.pth = DF{-0.5f * d2H_t.hi, -0.5f * d2H_t.lo};
+}
+
+// One out-of-line copy (descriptor by pointer, the rest by value).
+static __device__ __noinline__ FlowDF table_flow_df_call(const ImageDesc* d, RayDF R, StateDF y) {
+    FlowDF o;
+    table_flow_df(*d, R, y, o.f, o.H);
+    return o;
+}
+
+// METRIC 0: closed-form Kerr, 1: table.
+template <int METRIC>
+__device__ __forceinline__ void flow_df(const ImageDesc& d, const KerrDF& k, const RayDF& R, const StateDF& y,
+                                        StateDF& f, DF& H) {
+    static_assert(METRIC == 0 || METRIC == 1, "the double-float kernels take one metric kind per launch");
+    if constexpr (METRIC == 0) {
+        kerr_flow_df(k, R, y, f, H);
+    } else {
+        const FlowDF o = table_flow_df_call(&d, R, y);
+        f = o.f;
+        H = o.H;
+    }
 }
 
 }  // namespace tt

@@ -20,18 +20,23 @@ struct ImageDesc {
     double alpha_min, dalpha, beta_min, dbeta;
     // observer
     double r_obs, theta_obs;
+    // the flags, packed (the batch of descriptors travels as kernel parameters):
+    // metric kind (0 Kerr, 1 table), observer tetrad resolved (below), disk
+    // enabled, crossings to record, Doppler factor in the redshift
+    int kind;
+    int8_t obs_ready, disk, max_cross, doppler;
     // ZAMO tetrad at the observer, resolved on the host for the closed-form
     // metric (obs_ready = 1): g_tt, g_tphi, g_rr, g_thth, g_phiphi, omega/N,
     // 1/N, 1/sqrt(g_rr), 1/sqrt(g_thth), 1/sqrt(g_phiphi)
-    int obs_ready;
     double obs_g[5];
     double obs_omN, obs_iN, obs_ir, obs_ith, obs_iph;
     // metric
-    int kind;                     // 0 Kerr, 1 table
     double M, a;
     const double* table;          // device nodes in local-slope form (see tt_capi.cu)
+    const float2* table_df;       // the same nodes as double-float (hi, lo) pairs
     int nr, nth;
     double u0, du, dth;           // ln r_min, ln-spacing, theta spacing
+    float2 u0_df, idu_df, idth_df;          // u0, 1/du, 1/dth as double-float (hi, lo)
     // events
     double r_capture;             // r_h (1 + horizon_eps)
     double r_escape;              // escape_factor * r_obs
@@ -39,7 +44,6 @@ struct ImageDesc {
     double th_pole;               // mixed paths: double-float steps within this angle of the axis
     double r_plus, r_minus;       // Kerr horizons (mixed path: Delta = (r - r_+)(r - r_-))
     // disk
-    int disk, max_cross, doppler;
     double r_in, r_out, mdot;
     double fx0, fa;               // x0 = sqrt(r_isco / M), a / M
     double fxr[3], fcoef[3], flog0[3];   // roots x_i, their coefficients, log(x0 - x_i)

@@ -80,6 +80,7 @@ cudaError_t launch_trace(const ImageDesc* descs, int n, long long total_rays, in
         if (sol.method == 4) return launch_rk<4>(descs, n, total_rays, metric_mode, sol, shape, queue, stream);
         return cudaErrorInvalidValue;
     }
+    if (sol.precision == 3) return launch_df(descs, n, total_rays, metric_mode, sol, shape, queue, stream);
     if (sol.precision != 0) {
         if (metric_mode != 0) return cudaErrorInvalidValue;
         return launch_mixed(descs, n, total_rays, sol, shape, queue, stream);

@@ -24,7 +24,6 @@ static cudaError_t launch_mixed_n(const ImageDesc* descs, int n, long long total
 
 cudaError_t launch_mixed(const ImageDesc* descs, int n, long long total, const SolverDesc& sol,
                          const LaunchShape& shape, unsigned long long* queue, cudaStream_t stream) {
-    if (sol.precision == 3) return launch_df(descs, n, total, sol, shape, queue, stream);
     if (shape.block == 128) return cudaErrorInvalidValue;      // spills: not built
     if (n == 1) return launch_mixed_n<1>(descs, n, total, sol, shape, queue, stream);
     return launch_mixed_n<kMaxImagesPerLaunch>(descs, n, total, sol, shape, queue, stream);

@@ -635,7 +635,8 @@ __device__ bool init_ray(Lane& L, const ImageDesc* d_ptr, long long q, const Sol
         L.h = (sol.h0 > 0.0) ? sol.h0 : initial_step64<METRIC>(d, L.kk, L.R, L.y, L.k1, sol.atol, sol.rtol);
         L.k64_ok = true;
     } else {
-        // mixed paths: FP32 flow and starting step; |H(y0)| is ~1e-16 and not sampled
+        // mixed paths: FP32 flow and starting step, |H(y0)| (~1e-16) not sampled;
+        // double-float path: the FP64 flow and starting step
         L.k64_ok = false;
         L.Rf = to_float(L.R, d.M);
         L.Mf = (float)d.M;
@@ -647,11 +648,6 @@ __device__ bool init_ray(Lane& L, const ImageDesc* d_ptr, long long q, const Sol
         L.fp64f = (float)d.r_fp64;
         L.thpf = (float)d.th_pole;
         L.lamf = 0.0f;
-        const StateF yf = {(float)L.y.r, (float)L.y.th, (float)L.y.pr, (float)L.y.pth};
-        const float dr0 = (float)(L.y.r - d.r_plus);
-        float H0;
-        kerr_flow32(L.Mf, L.a2f, L.rpmf, L.Rf, yf, dr0, L.k1f, H0);
-        L.k32_ok = true;
         if (sol.precision == 3) {
             // double-float path: the FP64 path's starting step (once per ray), so
             // that both begin the same step sequence
@@ -663,6 +659,11 @@ __device__ bool init_ray(Lane& L, const ImageDesc* d_ptr, long long q, const Sol
             L.hf = (float)((sol.h0 > 0.0) ? sol.h0
                                          : initial_step64<METRIC>(d, L.kk, L.R, L.y, L.k1, sol.atol, sol.rtol));
         } else {
+            const StateF yf = {(float)L.y.r, (float)L.y.th, (float)L.y.pr, (float)L.y.pth};
+            const float dr0 = (float)(L.y.r - d.r_plus);
+            float H0;
+            kerr_flow32(L.Mf, L.a2f, L.rpmf, L.Rf, yf, dr0, L.k1f, H0);
+            L.k32_ok = true;
             L.hf = (sol.h0 > 0.0) ? (float)sol.h0 : initial_step32(L, yf, dr0, (float)sol.atol, (float)sol.rtol);
         }
         L.h = (double)L.hf;
@@ -1024,7 +1025,7 @@ __device__ int step_ray32(Lane& L, StateF& yhi, const SolverDesc& sol) {
 // step-size control run in FP32.  ACC 0: the state is the FP64 L.y;
 // ACC 1: the FP32 pair (yhi, L.lo).
 // ---------------------------------------------------------------------------
-template <int ACC, bool FULL>
+template <int METRIC, int ACC, bool FULL>
 __device__ int step_ray_df(Lane& L, StateF& yhi, const SolverDesc& sol) {
     constexpr int PREC = FULL ? 3 : ACC + 1;
     const ImageDesc& d = *L.d;
@@ -1051,7 +1052,7 @@ __device__ int step_ray_df(Lane& L, StateF& yhi, const SolverDesc& sol) {
     DF Hs;
     StateDF k1;
     if (!L.kdf_ok) {
-        kerr_flow_df(kd, rd, y, k1, Hs);
+        flow_df<METRIC>(d, kd, rd, y, k1, Hs);
     } else {
         k1 = StateDF{DF{L.k1f.r, L.k1lo.r}, DF{L.k1f.th, L.k1lo.th}, DF{L.k1f.pr, L.k1lo.pr},
                      DF{L.k1f.pth, L.k1lo.pth}};
@@ -1062,7 +1063,7 @@ __device__ int step_ray_df(Lane& L, StateF& yhi, const SolverDesc& sol) {
     ys.th = S(th);                                                                    \
     ys.pr = S(pr);                                                                    \
     ys.pth = S(pth);                                                                  \
-    kerr_flow_df(kd, rd, ys, dst, Hs);
+    flow_df<METRIC>(d, kd, rd, ys, dst, Hs);
     if constexpr (FULL) {
         constexpr DF A21 = df_const(a21), A31 = df_const(a31), A32 = df_const(a32);
         constexpr DF A41 = df_const(a41), A42 = df_const(a42), A43 = df_const(a43);
@@ -1123,7 +1124,7 @@ __device__ int step_ray_df(Lane& L, StateF& yhi, const SolverDesc& sol) {
     }
 #undef TT_DS
     DF Hn;
-    kerr_flow_df(kd, rd, yn, k7, Hn);
+    flow_df<METRIC>(d, kd, rd, yn, k7, Hn);
     // The error estimate h sum_i e_i k_i is a small difference of nearly equal
     // stage flows (sum_i e_i = 0): at tolerances near 1e-10 it is formed in
     // double-float with double-float weights (FULL), else FP32 rounding noise in
@@ -1165,7 +1166,7 @@ __device__ int step_ray_df(Lane& L, StateF& yhi, const SolverDesc& sol) {
         const bool s1 = !pair_below(pi2h, pi2l, yn.th.hi, yn.th.lo);    // and after
         if (d.disk && s0 != s1) {
             const State yc = (ACC == 0) ? L.y : pair_to64(yhi, L.lo);
-            note_crossing<0, PREC>(L, yc, sol);
+            note_crossing<METRIC, PREC>(L, yc, sol);
         }
         if constexpr (ACC == 0) {
             L.y = State{df_to64(yn.r), df_to64(yn.th), df_to64(yn.pr), df_to64(yn.pth)};
@@ -1196,6 +1197,36 @@ __device__ int step_ray_df(Lane& L, StateF& yhi, const SolverDesc& sol) {
         L.last_rej = true;
     }
     return -1;
+}
+
+// A double-float-path step near the horizon or the axis of a tabulated metric,
+// in FP64: there the interpolated D = g_tt g_phiphi - g_tphi^2 (-Delta sin^2
+// theta for Kerr) goes to zero, and W / D (and its derivatives) lose the
+// double-float's digits in proportion; the FP32-pair state, step size and
+// affine parameter are carried over exactly and back.
+template <int METRIC>
+__device__ int step_zone64(Lane& L, StateF& yhi, const SolverDesc& sol) {
+    L.y = pair_to64(yhi, L.lo);
+    if (!L.k64_ok) {
+        double H;
+        flow64<METRIC>(*L.d, L.kk, L.R, L.y, L.k1, H);
+        L.k64_ok = true;
+    }
+    L.h = (double)L.hf;
+    L.lam = (double)L.lamf;
+    const int code = step_ray64<METRIC, 3>(L, sol);
+    split_state(L.y, yhi, L.lo);
+    L.hf = (float)L.h;
+    L.lamf = (float)L.lam;
+    L.kdf_ok = false;
+    return code;
+}
+
+// Steps of the double-float table path that run in FP64 (the zones of the
+// solver's fp64_radius_factor and fp64_pole_sin).
+__device__ __forceinline__ bool in_zone(const Lane& L, const StateF& yhi) {
+    const float axis = fabsf(fmaf(-rintf(yhi.th * 0.318309886f), 3.14159274f, yhi.th));
+    return (yhi.r < L.fp64f) || (axis < L.thpf);
 }
 
 // FP64 |H| at the lane's current state (mixed-path monitor).
@@ -1229,6 +1260,7 @@ __device__ __forceinline__ void trace_loop(const ImageDesc* descs, int n_desc, l
     constexpr int ACC = (PREC >= 2) ? 1 : 0;
     if constexpr (PREC != 0) {
         df_sincos_table(s_df_tab);
+        if constexpr (METRIC == 1) df_log_table(s_df_ln);
         __syncthreads();
     }
     const int lane = threadIdx.x & 31;
@@ -1276,15 +1308,21 @@ __device__ __forceinline__ void trace_loop(const ImageDesc* descs, int n_desc, l
         }
         ++iter;
         // ---- step phases ---------------------------------------------------
-        if (PREC == 3) {
+        if constexpr (PREC == 3) {
             if (st == kRun) {
-                const int code = step_ray_df<1, true>(L, yhi, sol);
+                int code;
+                if constexpr (METRIC == 1) {
+                    code = in_zone(L, yhi) ? step_zone64<METRIC>(L, yhi, sol)
+                                           : step_ray_df<METRIC, 1, true>(L, yhi, sol);
+                } else {
+                    code = step_ray_df<METRIC, 1, true>(L, yhi, sol);
+                }
                 if (code >= 0) {
                     L.code = code;
                     st = kDone;
                 }
             }
-        } else if (PREC == 0) {
+        } else if constexpr (PREC == 0) {
             if (st == kRun) {
                 const int code = step_ray64<METRIC, 0, METHOD>(L, sol);
                 if (code >= 0) {
@@ -1310,7 +1348,7 @@ __device__ __forceinline__ void trace_loop(const ImageDesc* descs, int n_desc, l
                 wait64 = run64 ? 0 : wait64 + 1;
                 if (run64 && want64) {
                     // the extended-precision step, in double-float on the FP32 pipe
-                    const int code = step_ray_df<ACC, false>(L, yhi, sol);
+                    const int code = step_ray_df<METRIC, ACC, false>(L, yhi, sol);
                     if (code >= 0) {
                         L.code = code;
                         st = kDone;
@@ -1380,7 +1418,7 @@ void fill_params(LaunchParams<N>& p, const ImageDesc* descs, int n, long long to
 // (tt_kernel_df.cu).
 cudaError_t launch_mixed(const ImageDesc* descs, int n, long long total, const SolverDesc& sol,
                          const LaunchShape& shape, unsigned long long* queue, cudaStream_t stream);
-cudaError_t launch_df(const ImageDesc* descs, int n, long long total, const SolverDesc& sol,
+cudaError_t launch_df(const ImageDesc* descs, int n, long long total, int metric_mode, const SolverDesc& sol,
                       const LaunchShape& shape, unsigned long long* queue, cudaStream_t stream);
 
 }  // namespace tt

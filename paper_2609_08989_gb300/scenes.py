@@ -62,8 +62,9 @@ class Scene:
     escape_factor: float = 1.1
     refine: int = REFINE_HENON
     method: int = DOPRI5              # integrator (Verlet: fixed step h0 > 0)
-    fp64_radius_factor: float = 0.0   # mixed paths: extended-precision steps below factor * r_h (0: 2, < 0: none)
-    fp64_pole_sin: float = 0.0        # mixed paths: extended-precision steps where sin(theta) < this (0: 0.3, < 0: none)
+    fp64_radius_factor: float = 0.0   # mixed paths, double-float on a table: extended-precision steps below
+                                      # factor * r_h (0: 2, < 0: none)
+    fp64_pole_sin: float = 0.0        # the same, where sin(theta) < this (0: 0.3 mixed, none on a table; < 0: none)
     # disk
     disk_enabled: int = 0
     r_in: float = 0.0            # <= 0: ISCO

@@ -1,7 +1,9 @@
 // Accuracy of the library's double-float arithmetic (tt_df.cuh) against FP64
 // on seeded random inputs: sin/cos over several periods, the reciprocal, and
-// the Kerr flow and Hamiltonian against the FP64 flow of the same state.
-// Prints one line per quantity: name, max error, error measure.
+// the Kerr flow and Hamiltonian against the FP64 flow of the same state, and
+// the logarithm of the tabulated metric's radial coordinate.
+// Prints one line per quantity: name, max error, error measure.  H is a sum of
+// terms that cancel, so its error is measured against the size of those terms.
 #include <cmath>
 #include <cstdio>
 #include <vector>
@@ -12,6 +14,7 @@ using namespace tt;
 
 __global__ void k_accuracy(int n, const double* in, double* out) {
     df_sincos_table(s_df_tab);
+    df_log_table(s_df_ln);
     __syncthreads();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -29,7 +32,7 @@ __global__ void k_accuracy(int n, const double* in, double* out) {
     kerr_flow_df(make_kerr_df(k), make_ray_df(R), yd, fd, Hd);
     DF s, c;
     df_sincos(df_of(th), s, c);
-    double* o = out + 16 * i;
+    double* o = out + 20 * i;
     o[0] = f.r;   o[1] = df_to64(fd.r);
     o[2] = f.th;  o[3] = df_to64(fd.th);
     o[4] = f.pr;  o[5] = df_to64(fd.pr);
@@ -38,11 +41,17 @@ __global__ void k_accuracy(int n, const double* in, double* out) {
     o[10] = sin(th); o[11] = df_to64(s);
     o[12] = cos(th); o[13] = df_to64(c);
     o[14] = 1.0 / x; o[15] = df_to64(df_rcp(df_of(x)));
+    o[16] = log(x);  o[17] = df_to64(df_log(df_of(x)));
+    // the terms of 2 Sigma H: Delta pr^2, pth^2, (pph + a sin^2 pt)^2 / sin^2, ((r^2 + a^2) pt + a pph)^2 / Delta
+    const double sn = sin(th), cs = cos(th), s2 = sn * sn;
+    const double Sig = r * r + a * a * cs * cs, Del = r * r - 2.0 * r + a * a;
+    const double t3 = (pph + a * s2 * pt), t4 = (r * r + a * a) * pt + a * pph;
+    o[18] = (Del * pr * pr + pth * pth + t3 * t3 / s2 + t4 * t4 / fabs(Del)) / (2.0 * Sig);
 }
 
 int main() {
     const int n = 8192;
-    std::vector<double> in(8 * n), out(16 * n);
+    std::vector<double> in(8 * n), out(20 * n);
     unsigned long long st = 2609;
     auto rnd = [&]() {
         st = st * 6364136223846793005ULL + 1442695040888963407ULL;
@@ -75,18 +84,19 @@ int main() {
     cudaMemcpy(out.data(), dout, out.size() * 8, cudaMemcpyDeviceToHost);
     cudaFree(din);
     cudaFree(dout);
-    // relative error for the flow components (against max(|value|, 1e-6 |scale|)),
-    // absolute for H, sin and cos, relative for the reciprocal
-    const char* names[] = {"flow_r", "flow_th", "flow_pr", "flow_pth", "H", "sin", "cos", "rcp"};
-    for (int q = 0; q < 8; ++q) {
+    // relative error for the flow components and the reciprocal, absolute for
+    // sin, cos and log, and for H relative to the size of its terms
+    const char* names[] = {"flow_r", "flow_th", "flow_pr", "flow_pth", "H", "sin", "cos", "rcp", "log"};
+    for (int q = 0; q < 9; ++q) {
         double worst = 0.0;
         for (int i = 0; i < n; ++i) {
-            const double a = out[16 * i + 2 * q], b = out[16 * i + 2 * q + 1];
+            const double a = out[20 * i + 2 * q], b = out[20 * i + 2 * q + 1];
             double d = std::fabs(a - b);
             if (q < 4 || q == 7) d /= std::fabs(a) + 1e-300;
+            if (q == 4) d /= out[20 * i + 18];
             if (d > worst) worst = d;
         }
-        std::printf("%s %.6e %s\n", names[q], worst, (q < 4 || q == 7) ? "rel" : "abs");
+        std::printf("%s %.6e %s\n", names[q], worst, (q == 4) ? "rel_terms" : (q < 4 || q == 7) ? "rel" : "abs");
     }
     return 0;
 }

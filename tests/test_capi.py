@@ -123,15 +123,18 @@ def test_batch_reports_bad_image_without_gpu():
     assert st == T.TT_EINVAL and list(status) == [T.TT_EINVAL, T.TT_EINVAL]
 
 
-def test_batch_mixing_metric_kinds_refused_for_ck_and_f():
+def test_batch_mixing_metric_kinds_refused_for_one_kind_kernels():
     sc = scenes.kerr_disk(16)
     imgs = (T.TTImage * 2)()
     for i in range(2):
         m, o, cam, s, d, out = _args(sc, **({"m__kind": 1} if i == 1 else {}))
         imgs[i].metric, imgs[i].obs, imgs[i].cam, imgs[i].disk, imgs[i].out = m, o, cam, d, out
     status = (C.c_int * 2)(-7, -7)
-    for method in (1, 2, 3, 4):
-        s = T.solver_struct(sc.replace(method=method, h0=0.01))
+    # the other integrators, and the double-float path, take one metric kind per launch
+    solvers = [sc.replace(method=method, h0=0.01) for method in (1, 2, 3, 4)]
+    solvers.append(sc.replace(precision=scenes.DOUBLE_FLOAT))
+    for sv in solvers:
+        s = T.solver_struct(sv)
         for fn in (T.lib().tartarus_trace_batch, T.lib().tartarus_trace_batch_noalloc):
             assert fn(imgs, 2, C.byref(s), None, status, None) == T.TT_EUNSUPPORTED
             assert list(status) == [-7, -7]          # refused before any image was looked at

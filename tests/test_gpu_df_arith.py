@@ -1,8 +1,9 @@
 """Accuracy of the double-float arithmetic the double-float path and the mixed
 paths' zone steps use: a small CUDA program (tests/cuda/df_accuracy.cu, built
 here with nvcc for sm_103a against the library's own device headers) compares
-double-float sin/cos, reciprocal, Kerr flow and Hamiltonian with their FP64
-values on 8192 seeded inputs, including polar angles beyond (0, pi)."""
+double-float sin/cos, reciprocal, logarithm, Kerr flow and Hamiltonian with
+their FP64 values on 8192 seeded inputs, including polar angles beyond (0, pi)
+and arguments of the logarithm from 2^-30 to 2^30."""
 import os
 import subprocess
 
@@ -17,7 +18,8 @@ CSRC = os.path.join(ROOT, "paper_2609_08989_gb300", "csrc")
 # double-float carries ~48 bits (2^-48 = 3.6e-15; the reciprocal within 2^-46): sin/cos to the absolute precision of theta
 # itself (|theta| <= 8 here: 2^-48 x 8 ~ 3e-14); the flow components relative
 # to their own size except where they are a cancelled difference
-BOUNDS = {"sin": 1e-13, "cos": 1e-13, "rcp": 5e-14, "flow_th": 1e-12, "flow_r": 1e-11}
+BOUNDS = {"sin": 1e-13, "cos": 1e-13, "rcp": 5e-14, "flow_th": 1e-12, "flow_r": 1e-11,
+          "log": 2e-13}      # |ln x| <= 21 here: 21 x 2^-48 = 7.5e-14
 
 
 def test_double_float_accuracy(tmp_path):
@@ -37,5 +39,8 @@ def test_double_float_accuracy(tmp_path):
     print(got)
     for name, bound in BOUNDS.items():
         assert got[name] < bound, (name, got[name])
-    # H: a sum of terms that cancel; absolute error stays far below the 1e-6 |H| target
-    assert got["H"] < 1e-8
+    # H: a sum of terms that cancel (up to ~1e8 near the axis here), measured
+    # against the size of those terms.  Within 1 % of r_+ Delta = r (r - 2M) + a^2
+    # itself cancels ~10^3-fold, so the pair's 2^-48 becomes ~1e-11 there
+    # (FP64 loses the same factor, from 2^-53)
+    assert got["H"] < 1e-10

@@ -85,3 +85,43 @@ def test_same_steps_as_fp64_path(T):
     b = run(T, sc.replace(precision=scenes.DOUBLE_FLOAT))
     assert (a["code"] == b["code"]).mean() > 0.9999
     assert ((a["steps"] == b["steps"]) & (a["rejects"] == b["rejects"])).mean() > 0.995
+
+
+# The tabulated metric, at the FP64 table path's bars: at rtol 1e-12 the
+# interpolated flow (its slopes cancel ~10^3-fold) carries rounding of the order
+# of the tolerance, so step decisions flip between any two correct
+# implementations; identical step sequences agree to 1e-8, diverged ones to 1e-6,
+# well inside the interpolant's own ~1e-6 distance from the closed-form metric.
+# |H| maxima of captured rays (set by rounding just outside the FP64 zone at
+# 2 r_h) within the double-float factor of the closed-form tests.
+TABLE_BARS = dict(rel=1e-8, min_same_steps=0.0, rel_diverged=1e-6, h_ratio_only=True, h_ratio=32.0)
+
+
+def _table_scene(orc, n):
+    a = 0.998
+    rh = 1.0 + np.sqrt(1.0 - a * a)
+    return scenes.table_kerr(n, table=orc.kerr_table(1.0, a, 512, 256, rh, 1000.0))
+
+
+def test_table_metric(T, orc):
+    sc = _table_scene(orc, 48).replace(precision=scenes.DOUBLE_FLOAT)
+    got = run(T, sc)
+    rep = parity.compare(orc, sc, got, orc.trace(sc), np.arange(sc.npix), **TABLE_BARS)
+    print("double-float table 48^2:", rep)
+    # against the FP64 table path: the same outcome on nearly every ray, and
+    # about as many steps (the interpolated flow's rounding sets no step size)
+    f64 = run(T, sc.replace(precision=scenes.FP64))
+    assert (f64["code"] == got["code"]).mean() > 0.99
+    ratio = got["steps"].sum() / f64["steps"].sum()
+    print("steps double-float / FP64: %.4f" % ratio)
+    assert 0.95 < ratio < 1.1
+
+
+def test_table_ragged_range(T, orc):
+    # an even nx: on an odd grid the alpha = 0 column's rays (p_phi = 0) pass
+    # through the polar axis, where the interpolated W / D is 0/0 and every
+    # implementation's step size collapses (the oracle takes 6e4 - 1.5e5 steps
+    # there and ends some at max_steps or h_min): no two agree on those
+    sc = _table_scene(orc, 60).replace(ny=37, precision=scenes.DOUBLE_FLOAT)
+    got = run(T, sc, pix_begin=517, pix_count=1111)
+    parity.compare(orc, sc, got, orc.trace(sc, pix_begin=517, npix=1111), np.arange(517, 517 + 1111), **TABLE_BARS)
