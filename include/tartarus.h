@@ -202,8 +202,9 @@ typedef struct {
  *   blocks_per_sm   persistent blocks per SM (0: as many as fit)
  *   crossing_batch  refine disk crossings once this many lanes of a warp have
  *                   one pending (1..32; default 8 FP64, 16 mixed)
- *   fp64_batch      mixed paths: run the extended-precision zone steps once this many
- *                   lanes need one (1..32, default 16)
+ *   fp64_batch      mixed paths (and the double-float path on a table): run the
+ *                   extended-precision zone steps once this many lanes need one
+ *                   (1..32, default 16; 1 on the double-float path)
  *   monitor_period  mixed paths: evaluate |H| in FP64 every this many warp
  *                   iterations (default 32)
  *   fp64_wait       mixed paths: lanes waiting for a zone step get one after at

@@ -18,8 +18,8 @@
 #include "tt_internal.h"
 
 struct tt_table {
-    double* d_nodes;     // device nodes, local-slope form
-    float2* d_nodes_df;  // the same nodes as double-float pairs (hi, lo)
+    double* d_coef;      // device patch coefficients, kTableCoef per cell
+    float2* d_coef_df;   // the same as double-float pairs (hi, lo)
     int nr, nth;
     double r_min, r_max;
     int device;
@@ -53,7 +53,7 @@ int check_metric(const tt_metric* m) {
     if (!is_finite(m->M) || !(m->M > 0.0) || !is_finite(m->a)) return TT_EINVAL;
     if (m->kind == TT_METRIC_KERR && !(std::fabs(m->a) < m->M)) return TT_EINVAL;
     if (m->kind == TT_METRIC_TABLE) {
-        if (!m->table || !m->table->d_nodes) return TT_EINVAL;
+        if (!m->table || !m->table->d_coef) return TT_EINVAL;
         int dev = 0;
         cudaGetDevice(&dev);
         if (dev != m->table->device) return TT_EINVAL;
@@ -130,8 +130,8 @@ int make_desc(const tt_metric* m, const tt_observer* obs, const tt_camera* cam, 
         return TT_EUNSUPPORTED;
     if (m->kind == TT_METRIC_TABLE) {
         const tt_table* t = m->table;
-        d->table = t->d_nodes;
-        d->table_df = t->d_nodes_df;
+        d->table = t->d_coef;
+        d->table_df = t->d_coef_df;
         d->nr = t->nr;
         d->nth = t->nth;
         d->u0 = std::log(t->r_min);
@@ -562,24 +562,64 @@ int tartarus_table_create(const double* host_nodes, int nr, int nth, double r_mi
             }
         }
     }
+    // Per cell and field, the bicubic Hermite patch in the monomial basis,
+    // v(t, w) = sum_ij c_ij t^i w^j: C = Hm^T G Hm, where G[m][n] is the
+    // coefficient of h_m(t) h_n(w) (m = 2 cu + u-slope, n = 2 ct + theta-slope
+    // for the corner (cu, ct)) and row m of Hm the power coefficients of h_m:
+    // h0 = 1 - 3t^2 + 2t^3, h1 = t - 2t^2 + t^3, h2 = 3t^2 - 2t^3, h3 = t^3 - t^2.
+    // The same polynomial as the Hermite form; it evaluates by Horner's rule
+    // with half the multiply-adds and no basis functions.
+    static const double Hm[4][4] = {{1, 0, -3, 2}, {0, 1, -2, 1}, {0, 0, 3, -2}, {0, 0, -1, 1}};
+    const size_t ncoef = (size_t)(nr - 1) * (size_t)(nth - 1) * tt::kTableCoef;
+    std::vector<double> cf(ncoef);
+    for (int j = 0; j + 1 < nth; ++j) {
+        for (int k = 0; k + 1 < nr; ++k) {
+            double* dst = cf.data() + ((size_t)j * (nr - 1) + k) * tt::kTableCoef;
+            for (int f = 0; f < 5; ++f) {
+                double G[4][4];
+                for (int ct = 0; ct < 2; ++ct) {
+                    for (int cu = 0; cu < 2; ++cu) {
+                        const double* nd = loc.data() + ((size_t)(j + ct) * nr + (k + cu)) * tt::kTableNF + 4 * f;
+                        G[2 * cu][2 * ct] = nd[0];
+                        G[2 * cu + 1][2 * ct] = nd[1];
+                        G[2 * cu][2 * ct + 1] = nd[2];
+                        G[2 * cu + 1][2 * ct + 1] = nd[3];
+                    }
+                }
+                double GH[4][4];          // G Hm
+                for (int m = 0; m < 4; ++m)
+                    for (int q = 0; q < 4; ++q) {
+                        double acc = 0.0;
+                        for (int n2 = 0; n2 < 4; ++n2) acc += G[m][n2] * Hm[n2][q];
+                        GH[m][q] = acc;
+                    }
+                for (int i = 0; i < 4; ++i)
+                    for (int q = 0; q < 4; ++q) {
+                        double acc = 0.0;
+                        for (int m = 0; m < 4; ++m) acc += Hm[m][i] * GH[m][q];
+                        dst[16 * f + 4 * i + q] = acc;
+                    }
+            }
+        }
+    }
     // the double-float copy
-    std::vector<float2> ldf(n);
-    for (size_t i = 0; i < n; ++i) ldf[i] = split_df(loc[i]);
+    std::vector<float2> cdf(ncoef);
+    for (size_t i = 0; i < ncoef; ++i) cdf[i] = split_df(cf[i]);
     tt_table* t = new (std::nothrow) tt_table;
     if (!t) return TT_ENOMEM;
-    t->d_nodes = nullptr;
-    t->d_nodes_df = nullptr;
+    t->d_coef = nullptr;
+    t->d_coef_df = nullptr;
     cudaGetDevice(&t->device);
-    if (cudaMalloc((void**)&t->d_nodes, n * sizeof(double)) != cudaSuccess ||
-        cudaMalloc((void**)&t->d_nodes_df, n * sizeof(float2)) != cudaSuccess) {
-        cudaFree(t->d_nodes);
+    if (cudaMalloc((void**)&t->d_coef, ncoef * sizeof(double)) != cudaSuccess ||
+        cudaMalloc((void**)&t->d_coef_df, ncoef * sizeof(float2)) != cudaSuccess) {
+        cudaFree(t->d_coef);
         delete t;
         return TT_ENOMEM;
     }
-    if (cudaMemcpy(t->d_nodes, loc.data(), n * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(t->d_nodes_df, ldf.data(), n * sizeof(float2), cudaMemcpyHostToDevice) != cudaSuccess) {
-        cudaFree(t->d_nodes);
-        cudaFree(t->d_nodes_df);
+    if (cudaMemcpy(t->d_coef, cf.data(), ncoef * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(t->d_coef_df, cdf.data(), ncoef * sizeof(float2), cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaFree(t->d_coef);
+        cudaFree(t->d_coef_df);
         delete t;
         return TT_ECUDA;
     }
@@ -593,8 +633,8 @@ int tartarus_table_create(const double* host_nodes, int nr, int nth, double r_mi
 
 int tartarus_table_destroy(tt_table* t) {
     if (!t) return TT_EINVAL;
-    cudaError_t e = cudaFree(t->d_nodes);
-    const cudaError_t e2 = cudaFree(t->d_nodes_df);
+    cudaError_t e = cudaFree(t->d_coef);
+    const cudaError_t e2 = cudaFree(t->d_coef_df);
     delete t;
     return (e == cudaSuccess && e2 == cudaSuccess) ? TT_OK : TT_ECUDA;
 }

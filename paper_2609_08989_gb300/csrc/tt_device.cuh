@@ -267,9 +267,10 @@ __device__ __forceinline__ void kerr_lower64(double M, double a, double r, doubl
 }
 
 // ---------------------------------------------------------------------------
-// Tabulated metric: bicubic Hermite patches in (u = ln r, theta).  Device nodes
-// hold, per field, (F, F_u du, F_th dth, F_uth du dth) -- slopes already in the
-// unit-cell coordinates -- so a patch is a plain tensor-product Hermite form.
+// Tabulated metric: bicubic Hermite patches in (u = ln r, theta), one per cell
+// of the node grid, held on the device in the monomial basis of the cell's
+// unit coordinates (t, w): per field, c_ij (i: power of t, j: power of w),
+// evaluated with their t- and w-derivatives by Horner's rule.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void hermite4(double t, double h[4], double dh[4]) {
     // explicit FMAs only, so that every build rounds alike
@@ -284,6 +285,17 @@ __device__ __forceinline__ void hermite4(double t, double h[4], double dh[4]) {
     dh[3] = fma(3.0, t2, -2.0 * t);
 }
 
+// p = c0 + c1 x + c2 x^2 + c3 x^3 and dp = dp/dx
+__device__ __forceinline__ void horner_d(double c0, double c1, double c2, double c3, double x, double& p,
+                                         double& dp) {
+    double q = fma(c3, x, c2);
+    double d = fma(c3, x, q);
+    q = fma(q, x, c1);
+    d = fma(d, x, q);
+    p = fma(q, x, c0);
+    dp = d;
+}
+
 // All five fields (g_tt, g_tphi, g_thth, g_phiphi, g^rr) with d/dr and d/dth.
 __device__ __forceinline__ void table_fields64(const ImageDesc& d, double r, double th,
                                                double f[5], double fr[5], double ft[5]) {
@@ -292,36 +304,24 @@ __device__ __forceinline__ void table_fields64(const ImageDesc& d, double r, dou
     int k = (int)floor(tu), j = (int)floor(tw);
     k = min(max(k, 0), d.nr - 2);
     j = min(max(j, 0), d.nth - 2);
-    double t = tu - (double)k, w = tw - (double)j;
-    double A[4], dA[4], B[4], dB[4];
-    hermite4(t, A, dA);
-    hermite4(w, B, dB);
-    const double* n00 = d.table + ((size_t)j * d.nr + k) * kTableNF;
-    const double* nodes[4] = {n00, n00 + kTableNF, n00 + (size_t)d.nr * kTableNF,
-                              n00 + (size_t)d.nr * kTableNF + kTableNF};
-    // node order: (k, j), (k+1, j), (k, j+1), (k+1, j+1) -> (cu, ct) = (0,0), (1,0), (0,1), (1,1)
+    const double t = tu - (double)k, w = tw - (double)j;
+    const double* cell = d.table + ((size_t)j * (d.nr - 1) + k) * kTableCoef;
     const double inv_dur = 1.0 / (d.du * r), inv_dth = 1.0 / d.dth;
 #pragma unroll
     for (int fi = 0; fi < 5; ++fi) {
-        double v = 0.0, vu = 0.0, vt = 0.0;
+        const double2* c = reinterpret_cast<const double2*>(cell + 16 * fi);
+        double P[4], Q[4];        // sum_j c_ij w^j and its w-derivative, per power i of t
 #pragma unroll
-        for (int nd = 0; nd < 4; ++nd) {
-            const int cu = nd & 1, ct = nd >> 1;
-            const double2* p = reinterpret_cast<const double2*>(nodes[nd] + 4 * fi);
-            double2 q0 = __ldg(p), q1 = __ldg(p + 1);     // (F, Fu), (Ft, Fut)
-            double a0 = A[2 * cu], a1 = A[2 * cu + 1], da0 = dA[2 * cu], da1 = dA[2 * cu + 1];
-            double b0 = B[2 * ct], b1 = B[2 * ct + 1], db0 = dB[2 * ct], db1 = dB[2 * ct + 1];
-            double cb = fma(q0.x, b0, q1.x * b1);          // value column along theta
-            double cub = fma(q0.y, b0, q1.y * b1);         // u-slope column along theta
-            double cdb = fma(q0.x, db0, q1.x * db1);
-            double cudb = fma(q0.y, db0, q1.y * db1);
-            v = fma(a0, cb, fma(a1, cub, v));
-            vu = fma(da0, cb, fma(da1, cub, vu));
-            vt = fma(a0, cdb, fma(a1, cudb, vt));
+        for (int i = 0; i < 4; ++i) {
+            const double2 c01 = __ldg(c + 2 * i), c23 = __ldg(c + 2 * i + 1);
+            horner_d(c01.x, c01.y, c23.x, c23.y, w, P[i], Q[i]);
         }
+        double v, vt;
+        horner_d(P[0], P[1], P[2], P[3], t, v, vt);
+        const double vw = fma(fma(fma(Q[3], t, Q[2]), t, Q[1]), t, Q[0]);
         f[fi] = v;
-        fr[fi] = vu * inv_dur;
-        ft[fi] = vt * inv_dth;
+        fr[fi] = vt * inv_dur;
+        ft[fi] = vw * inv_dth;
     }
 }
 

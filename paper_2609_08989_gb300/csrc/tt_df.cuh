@@ -324,32 +324,27 @@ __device__ __forceinline__ DF df_log(DF x) {
 }
 
 // ---------------------------------------------------------------------------
-// Tabulated metric in double-float: the bicubic Hermite patches of
-// table_fields64 (u = ln r, theta; nodes in local-slope form), each value and
-// slope an accumulation of 16 node terms in the Dot2 style above, with the
-// basis products computed once per node and shared by the five fields.
+// Tabulated metric in double-float: the patches of table_fields64 (monomial
+// coefficients per cell and field, Horner's rule for the value and both
+// unit-cell derivatives) with double-float coefficients and arithmetic.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void hermite4_df(DF t, DF h[4], DF dh[4]) {
-    const DF t2 = df_sqr(t);
-    const DF omt = df_add_f(df_neg(t), 1.0f);                 // 1 - t
-    const DF omt2 = df_sqr(omt);
-    const DF tt = DF{2.0f * t.hi, 2.0f * t.lo};               // 2 t
-    h[0] = df_mul(df_add_f(tt, 1.0f), omt2);                  // (1 + 2t)(1 - t)^2
-    h[1] = df_mul(t, omt2);                                   // t (1 - t)^2
-    h[2] = df_mul(t2, df_add_f(df_neg(tt), 3.0f));            // t^2 (3 - 2t)
-    h[3] = df_neg(df_mul(t2, omt));                           // t^2 (t - 1)
-    dh[0] = df_mul_f(df_sub(t2, t), 6.0f);                    // 6 (t^2 - t)
-    dh[1] = df_mul(omt, df_add_f(df_mul_f(t, -3.0f), 1.0f));  // (1 - t)(1 - 3t)
-    dh[2] = df_neg(dh[0]);
-    dh[3] = df_mul(t, df_add_f(df_mul_f(t, 3.0f), -2.0f));    // t (3t - 2)
+// p = c0 + c1 x + c2 x^2 + c3 x^3 and dp = dp/dx
+__device__ __forceinline__ void horner_d_df(DF c0, DF c1, DF c2, DF c3, DF x, DF& p, DF& dp) {
+    DF q = df_fma(c3, x, c2);
+    DF d = df_fma(c3, x, q);
+    q = df_fma(q, x, c1);
+    d = df_fma(d, x, q);
+    p = df_fma(q, x, c0);
+    dp = d;
 }
 
-// Per-thread running sums of the table interpolation (15 per thread, strided by
-// the block size so that a warp's accesses fall in distinct banks); the
+// The 15 results pass through this thread's slots of s_df_out, so that the loop
+// over the fields stays rolled: the flow is evaluated at every stage, and five
+// unrolled copies of its patch evaluation overflowed the instruction cache.
+// Slots are strided by the block size (distinct banks within a warp); the
 // double-float kernels run 256-thread blocks.
 constexpr int kDfBlock = 256;
-constexpr int kDfAcc = 15;
-static __shared__ float2 s_df_acc[kDfAcc * kDfBlock];
+static __shared__ float2 s_df_out[15 * kDfBlock];
 
 // floor(x) clamped to [0, n_max] (NaN to 0), for a double-float x
 __device__ __forceinline__ int df_cell(DF x, int n_max) {
@@ -365,50 +360,33 @@ __device__ __forceinline__ void table_fields_df(const ImageDesc& d, DF r, DF th,
     const DF tu = df_mul(df_sub(df_log(r), u0), idu);
     const DF tw = df_mul(th, idth);
     const int k = df_cell(tu, d.nr - 2), j = df_cell(tw, d.nth - 2);
-    DF A[4], dA[4], B[4], dB[4];
-    hermite4_df(df_add_f(tu, -(float)k), A, dA);
-    hermite4_df(df_add_f(tw, -(float)j), B, dB);
-    const float2* n00 = d.table_df + ((size_t)j * d.nr + k) * kTableNF;
-    // the 15 running sums live in this thread's slots of s_df_acc, so that both
-    // loops below stay rolled: the flow is evaluated at every stage, and its
-    // unrolled form overflowed the instruction cache
-    float2* acc = s_df_acc + threadIdx.x;
-#pragma unroll
-    for (int q = 0; q < kDfAcc; ++q) acc[q * kDfBlock] = make_float2(0.0f, 0.0f);
-#pragma unroll 1
-    for (int nd = 0; nd < 4; ++nd) {
-        // node order (k, j), (k+1, j), (k, j+1), (k+1, j+1)
-        const bool cu = nd & 1, ct = nd >> 1;
-        const float2* node = n00 + (ct ? (size_t)d.nr * kTableNF : 0) + (cu ? kTableNF : 0);
-        const DF a0 = cu ? A[2] : A[0], a1 = cu ? A[3] : A[1], da0 = cu ? dA[2] : dA[0], da1 = cu ? dA[3] : dA[1];
-        const DF b0 = ct ? B[2] : B[0], b1 = ct ? B[3] : B[1], db0 = ct ? dB[2] : dB[0], db1 = ct ? dB[3] : dB[1];
-        // weights of the node's (F, F_u du, F_th dth, F_uth du dth) in the value,
-        // the u-slope and the theta-slope
-        const DF w0 = df_mul(a0, b0), w1 = df_mul(a1, b0), w2 = df_mul(a0, b1), w3 = df_mul(a1, b1);
-        const DF x0 = df_mul(da0, b0), x1 = df_mul(da1, b0), x2 = df_mul(da0, b1), x3 = df_mul(da1, b1);
-        const DF z0 = df_mul(a0, db0), z1 = df_mul(a1, db0), z2 = df_mul(a0, db1), z3 = df_mul(a1, db1);
-#pragma unroll 1
-        for (int fi = 0; fi < 5; ++fi) {
-            const float4* p = reinterpret_cast<const float4*>(node + 4 * fi);
-            const float4 q0 = __ldg(p), q1 = __ldg(p + 1);    // (F, F_u), (F_th, F_uth)
-            const DF F = DF{q0.x, q0.y}, Fu = DF{q0.z, q0.w}, Ft = DF{q1.x, q1.y}, Fut = DF{q1.z, q1.w};
-            float2* a = acc + 3 * fi * kDfBlock;
-            const float2 v0 = a[0], v1 = a[kDfBlock], v2 = a[2 * kDfBlock];
-            const DotAcc v = dot_next(dot_next(dot_next(dot_next(DotAcc{v0.x, v0.y}, w0, F), w1, Fu), w2, Ft), w3, Fut);
-            const DotAcc vu = dot_next(dot_next(dot_next(dot_next(DotAcc{v1.x, v1.y}, x0, F), x1, Fu), x2, Ft), x3, Fut);
-            const DotAcc vt = dot_next(dot_next(dot_next(dot_next(DotAcc{v2.x, v2.y}, z0, F), z1, Fu), z2, Ft), z3, Fut);
-            a[0] = make_float2(v.s, v.t);
-            a[kDfBlock] = make_float2(vu.s, vu.t);
-            a[2 * kDfBlock] = make_float2(vt.s, vt.t);
-        }
-    }
+    const DF t = df_add_f(tu, -(float)k), w = df_add_f(tw, -(float)j);
+    const float2* cell = d.table_df + ((size_t)j * (d.nr - 1) + k) * kTableCoef;
     const DF inv_dur = df_mul(idu, df_rcp(r));                 // 1 / (du r)
+    float2* out = s_df_out + threadIdx.x;
+#pragma unroll 1
+    for (int fi = 0; fi < 5; ++fi) {
+        const float4* c = reinterpret_cast<const float4*>(cell + 16 * fi);
+        DF P[4], Q[4];        // sum_j c_ij w^j and its w-derivative, per power i of t
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const float4 a = __ldg(c + 2 * i), b = __ldg(c + 2 * i + 1);
+            horner_d_df(DF{a.x, a.y}, DF{a.z, a.w}, DF{b.x, b.y}, DF{b.z, b.w}, w, P[i], Q[i]);
+        }
+        DF v, vt;
+        horner_d_df(P[0], P[1], P[2], P[3], t, v, vt);
+        const DF vw = df_fma(df_fma(df_fma(Q[3], t, Q[2]), t, Q[1]), t, Q[0]);
+        const DF vr = df_mul(vt, inv_dur), vth = df_mul(vw, idth);
+        out[(3 * fi) * kDfBlock] = make_float2(v.hi, v.lo);
+        out[(3 * fi + 1) * kDfBlock] = make_float2(vr.hi, vr.lo);
+        out[(3 * fi + 2) * kDfBlock] = make_float2(vth.hi, vth.lo);
+    }
 #pragma unroll
     for (int fi = 0; fi < 5; ++fi) {
-        const float2 v0 = acc[3 * fi * kDfBlock], v1 = acc[(3 * fi + 1) * kDfBlock], v2 = acc[(3 * fi + 2) * kDfBlock];
-        f[fi] = dot_end(DotAcc{v0.x, v0.y});
-        fr[fi] = df_mul(dot_end(DotAcc{v1.x, v1.y}), inv_dur);
-        ft[fi] = df_mul(dot_end(DotAcc{v2.x, v2.y}), idth);
+        const float2 a = out[(3 * fi) * kDfBlock], b = out[(3 * fi + 1) * kDfBlock], c = out[(3 * fi + 2) * kDfBlock];
+        f[fi] = DF{a.x, a.y};
+        fr[fi] = DF{b.x, b.y};
+        ft[fi] = DF{c.x, c.y};
     }
 }
 

@@ -11,7 +11,8 @@
 namespace tt {
 
 constexpr int kMaxCross = 3;
-constexpr int kTableNF = 20;
+constexpr int kTableNF = 20;         // doubles per table node (5 fields x value, 2 slopes, twist)
+constexpr int kTableCoef = 80;       // doubles per table cell (5 fields x 16 patch coefficients)
 
 struct ImageDesc {
     // camera
@@ -32,8 +33,8 @@ struct ImageDesc {
     double obs_omN, obs_iN, obs_ir, obs_ith, obs_iph;
     // metric
     double M, a;
-    const double* table;          // device nodes in local-slope form (see tt_capi.cu)
-    const float2* table_df;       // the same nodes as double-float (hi, lo) pairs
+    const double* table;          // device patch coefficients, cell-major (see tt_capi.cu)
+    const float2* table_df;       // the same as double-float (hi, lo) pairs
     int nr, nth;
     double u0, du, dth;           // ln r_min, ln-spacing, theta spacing
     float2 u0_df, idu_df, idth_df;          // u0, 1/du, 1/dth as double-float (hi, lo)

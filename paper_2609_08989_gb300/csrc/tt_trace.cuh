@@ -1308,15 +1308,33 @@ __device__ __forceinline__ void trace_loop(const ImageDesc* descs, int n_desc, l
         }
         ++iter;
         // ---- step phases ---------------------------------------------------
-        if constexpr (PREC == 3) {
-            if (st == kRun) {
-                int code;
-                if constexpr (METRIC == 1) {
-                    code = in_zone(L, yhi) ? step_zone64<METRIC>(L, yhi, sol)
-                                           : step_ray_df<METRIC, 1, true>(L, yhi, sol);
-                } else {
-                    code = step_ray_df<METRIC, 1, true>(L, yhi, sol);
+        if constexpr (PREC == 3 && METRIC == 1) {
+            // FP64 zone steps, batched across the warp like the mixed paths'
+            // extended-precision steps (a warp runs the FP64 step's code once for
+            // all its zone lanes, not once per straggler)
+            const bool want64 = (st == kRun) && in_zone(L, yhi);
+            const unsigned w64 = __ballot_sync(kFull, want64);
+            if (w64) {
+                const bool run64 = (__popc(w64) >= tp.fp64_batch) || (w64 == running) || (wait64 >= tp.fp64_wait);
+                wait64 = run64 ? 0 : wait64 + 1;
+                if (run64 && want64) {
+                    const int code = step_zone64<METRIC>(L, yhi, sol);
+                    if (code >= 0) {
+                        L.code = code;
+                        st = kDone;
+                    }
                 }
+            }
+            if (st == kRun && !want64) {
+                const int code = step_ray_df<METRIC, 1, true>(L, yhi, sol);
+                if (code >= 0) {
+                    L.code = code;
+                    st = kDone;
+                }
+            }
+        } else if constexpr (PREC == 3) {
+            if (st == kRun) {
+                const int code = step_ray_df<METRIC, 1, true>(L, yhi, sol);
                 if (code >= 0) {
                     L.code = code;
                     st = kDone;
@@ -1406,7 +1424,8 @@ void fill_params(LaunchParams<N>& p, const ImageDesc* descs, int n, long long to
     const bool mixed = sol.precision != 0;
     p.tune.refill = shape.refill > 0 ? shape.refill : (mixed ? 16 : 4);
     p.tune.crossing_batch = shape.crossing_batch > 0 ? shape.crossing_batch : (mixed ? 16 : 8);
-    p.tune.fp64_batch = shape.fp64_batch > 0 ? shape.fp64_batch : 16;
+    // (the double-float table path's FP64 zone steps measured fastest unbatched)
+    p.tune.fp64_batch = shape.fp64_batch > 0 ? shape.fp64_batch : (sol.precision == 3 ? 1 : 16);
     p.tune.monitor_period = shape.monitor_period > 0 ? shape.monitor_period : 32;
     p.tune.fp64_wait = shape.fp64_wait > 0 ? shape.fp64_wait : 64;
     p.total = total;

@@ -92,9 +92,11 @@ def test_same_steps_as_fp64_path(T):
 # of the tolerance, so step decisions flip between any two correct
 # implementations; identical step sequences agree to 1e-8, diverged ones to 1e-6,
 # well inside the interpolant's own ~1e-6 distance from the closed-form metric.
-# |H| maxima of captured rays (set by rounding just outside the FP64 zone at
-# 2 r_h) within the double-float factor of the closed-form tests.
-TABLE_BARS = dict(rel=1e-8, min_same_steps=0.0, rel_diverged=1e-6, h_ratio_only=True, h_ratio=32.0)
+# |H| maxima: at rtol 1e-12 a ray's drift off H = 0 is set by the rounding of
+# the interpolated flow, which carries the pair's 2^-48 instead of 2^-53, so the
+# maxima run up to ~2^5 above the oracle's (33x seen on captured rays, whatever
+# the radius of the FP64 zone); compared within 2^6, and bounded absolutely.
+TABLE_BARS = dict(rel=1e-8, min_same_steps=0.0, rel_diverged=1e-6, h_ratio_only=True, h_ratio=64.0)
 
 
 def _table_scene(orc, n):
@@ -108,6 +110,8 @@ def test_table_metric(T, orc):
     got = run(T, sc)
     rep = parity.compare(orc, sc, got, orc.trace(sc), np.arange(sc.npix), **TABLE_BARS)
     print("double-float table 48^2:", rep)
+    assert got["h_max"][got["code"] == 0].max() < 2e-8
+    assert got["h_max"].max() < 1e-5
     # against the FP64 table path: the same outcome on nearly every ray, and
     # about as many steps (the interpolated flow's rounding sets no step size)
     f64 = run(T, sc.replace(precision=scenes.FP64))
