@@ -328,13 +328,30 @@ __device__ __forceinline__ DF df_log(DF x) {
 // coefficients per cell and field, Horner's rule for the value and both
 // unit-cell derivatives) with double-float coefficients and arithmetic.
 // ---------------------------------------------------------------------------
-// p = c0 + c1 x + c2 x^2 + c3 x^3 and dp = dp/dx
+// x y + z without the closing renormalisation: lo may exceed half an ulp of hi
+// by a few bits, which the next multiply-add of a Horner chain absorbs (it takes
+// x.lo into an FP32 cross term, an error of ~2^-48 of the terms either way,
+// also where the sum cancels); chains are renormalised at their end.
+__device__ __forceinline__ DF df_fma_lazy(DF x, DF y, DF z) {
+    const float p = __fmul_rn(x.hi, y.hi);
+    float e = fmaf(x.hi, y.hi, -p);
+    e = fmaf(x.hi, y.lo, e);
+    e = fmaf(x.lo, y.hi, e);
+    const DF s = two_sum(p, z.hi);
+    return DF{s.hi, __fadd_rn(s.lo, __fadd_rn(e, z.lo))};
+}
+
+__device__ __forceinline__ DF df_norm(DF x) {
+    return two_sum(x.hi, x.lo);
+}
+
+// p = c0 + c1 x + c2 x^2 + c3 x^3 and dp = dp/dx (both left unnormalised)
 __device__ __forceinline__ void horner_d_df(DF c0, DF c1, DF c2, DF c3, DF x, DF& p, DF& dp) {
-    DF q = df_fma(c3, x, c2);
-    DF d = df_fma(c3, x, q);
-    q = df_fma(q, x, c1);
-    d = df_fma(d, x, q);
-    p = df_fma(q, x, c0);
+    DF q = df_fma_lazy(c3, x, c2);
+    DF d = df_fma_lazy(c3, x, q);
+    q = df_fma_lazy(q, x, c1);
+    d = df_fma_lazy(d, x, q);
+    p = df_fma_lazy(q, x, c0);
     dp = d;
 }
 
@@ -375,8 +392,9 @@ __device__ __forceinline__ void table_fields_df(const ImageDesc& d, DF r, DF th,
         }
         DF v, vt;
         horner_d_df(P[0], P[1], P[2], P[3], t, v, vt);
-        const DF vw = df_fma(df_fma(df_fma(Q[3], t, Q[2]), t, Q[1]), t, Q[0]);
-        const DF vr = df_mul(vt, inv_dur), vth = df_mul(vw, idth);
+        const DF vw = df_fma_lazy(df_fma_lazy(df_fma_lazy(Q[3], t, Q[2]), t, Q[1]), t, Q[0]);
+        v = df_norm(v);
+        const DF vr = df_mul(df_norm(vt), inv_dur), vth = df_mul(df_norm(vw), idth);
         out[(3 * fi) * kDfBlock] = make_float2(v.hi, v.lo);
         out[(3 * fi + 1) * kDfBlock] = make_float2(vr.hi, vr.lo);
         out[(3 * fi + 2) * kDfBlock] = make_float2(vth.hi, vth.lo);
