@@ -11,7 +11,9 @@ and ``trace_batch`` use the cached shape when no explicit ``tune`` is given.
 
 Workload classes: "fp64" (closed-form Kerr, FP64), "mixed" (FP32 stages with
 FP64 accumulation), "mixed_pair" (FP32-pair accumulation), "double_float"
-(every step in double-float), "table" (FP64 on a tabulated metric).  Results are identical for every shape; only time changes.
+(every step in double-float), "table" (FP64 on a tabulated metric),
+"table_double_float" (double-float on a tabulated metric).  Results are
+identical for every shape; only time changes.
 """
 from __future__ import annotations
 
@@ -35,11 +37,12 @@ SPACE: Dict[str, Dict[str, List[int]]] = {
 }
 SPACE["mixed_pair"] = SPACE["mixed"]
 SPACE["double_float"] = {"refill": [2, 4, 8, 16, 32], "crossing_batch": [4, 8, 16, 32], "blocks_per_sm": [0, 1, 2]}
+SPACE["table_double_float"] = {"refill": [2, 4, 8, 16, 32], "crossing_batch": [4, 8, 16, 32], "fp64_batch": [1, 4, 16]}
 
 
 def workload_class(sc) -> str:
     if sc.metric_kind == 1:
-        return "table"
+        return "table_double_float" if sc.precision == 3 else "table"
     return {0: "fp64", 1: "mixed", 2: "mixed_pair", 3: "double_float"}[sc.precision]
 
 
@@ -148,7 +151,9 @@ if __name__ == "__main__":
     todo = {"fp64": lambda: scenes.kerr_disk(1024),
             "mixed": lambda: scenes.kerr_disk_mixed(2048),
             "mixed_pair": lambda: scenes.kerr_disk_mixed(2048).replace(precision=scenes.MIXED_PAIR),
-            "double_float": lambda: scenes.kerr_disk(1024).replace(precision=scenes.DOUBLE_FLOAT)}
+            "double_float": lambda: scenes.kerr_disk(1024).replace(precision=scenes.DOUBLE_FLOAT),
+            "table": lambda: scenes.table_kerr_with_nodes(1024),
+            "table_double_float": lambda: scenes.table_kerr_with_nodes(1024).replace(precision=scenes.DOUBLE_FLOAT)}
     for name in which:
         sc = todo[name]()
         best, ms = tune_scene(sc, log=lambda m: print("  " + m, flush=True))

@@ -27,6 +27,7 @@ def test_classes_and_cache_roundtrip(monkeypatch, tmp_path):
     assert autotune.workload_class(scenes.kerr_disk_mixed(8)) == "mixed"
     assert autotune.workload_class(scenes.kerr_disk_mixed(8).replace(precision=scenes.MIXED_PAIR)) == "mixed_pair"
     assert autotune.workload_class(scenes.table_kerr(8)) == "table"
+    assert autotune.workload_class(scenes.table_kerr(8).replace(precision=scenes.DOUBLE_FLOAT)) == "table_double_float"
     cache = tmp_path / "tuned.json"
     monkeypatch.setattr(autotune, "CACHE", str(cache))
     monkeypatch.setattr(autotune, "_cache", None)
