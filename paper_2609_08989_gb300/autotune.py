@@ -29,8 +29,8 @@ _cache: Optional[dict] = None
 
 # search space per class (0 = the kernel's default)
 SPACE: Dict[str, Dict[str, List[int]]] = {
-    "fp64": {"block": [128, 256, 384], "reg_variant": [0, 1, 2], "refill": [1, 2, 4, 8, 16],
-             "crossing_batch": [2, 4, 8, 16, 24], "blocks_per_sm": [0, 1, 2]},
+    "fp64": {"block": [128, 256, 384], "reg_variant": [0, 1, 2], "refill": [1, 2, 4, 8, 16, 32],
+             "crossing_batch": [2, 4, 8, 16, 24, 32], "blocks_per_sm": [0, 1, 2]},
     "table": {"refill": [1, 2, 4, 8, 16], "crossing_batch": [2, 4, 8, 16, 24], "blocks_per_sm": [0, 1, 2]},
     "mixed": {"refill": [8, 16, 24, 32], "crossing_batch": [8, 16, 24, 32], "fp64_batch": [8, 16, 24, 32],
               "fp64_wait": [64, 256, 1024], "monitor_period": [16, 32, 64], "blocks_per_sm": [0, 1, 2]},
