@@ -106,6 +106,53 @@ __device__ __forceinline__ DF df_fma(DF x, DF y, DF z) {
     return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(e, z.lo)));
 }
 
+// "Lazy" forms: the same error-free parts without the closing renormalisation
+// (FastTwoSum).  Their lo may exceed half an ulp of hi by a few bits, and an
+// operation that takes such a value rounds x.lo y.hi in FP32: harmless after
+// a product of renormalised values (lo within ~2 ulps), but after a sum that
+// cancels lo can be a sizeable part of the value, and the product that takes
+// it then keeps only ~2^-48 of the sum's operands, not of its result.  So the
+// flows use lazy products of renormalised values and renormalise every sum;
+// Horner chains (terms of one size, error measured against them) are lazy
+// throughout.  A reciprocal's argument is renormalised.
+__device__ __forceinline__ DF df_mul_lazy(DF x, DF y) {
+    const float p = __fmul_rn(x.hi, y.hi);
+    float e = fmaf(x.hi, y.hi, -p);
+    e = fmaf(x.hi, y.lo, e);
+    e = fmaf(x.lo, y.hi, e);
+    return DF{p, e};
+}
+
+__device__ __forceinline__ DF df_sqr_lazy(DF x) {
+    const float p = __fmul_rn(x.hi, x.hi);
+    float e = fmaf(x.hi, x.hi, -p);
+    e = fmaf(__fadd_rn(x.hi, x.hi), x.lo, e);
+    return DF{p, e};
+}
+
+__device__ __forceinline__ DF df_add_lazy(DF x, DF y) {
+    const DF s = two_sum(x.hi, y.hi);
+    return DF{s.hi, __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo))};
+}
+
+__device__ __forceinline__ DF df_sub_lazy(DF x, DF y) {
+    return df_add_lazy(x, df_neg(y));
+}
+
+// x y + z
+__device__ __forceinline__ DF df_fma_lazy(DF x, DF y, DF z) {
+    const float p = __fmul_rn(x.hi, y.hi);
+    float e = fmaf(x.hi, y.hi, -p);
+    e = fmaf(x.hi, y.lo, e);
+    e = fmaf(x.lo, y.hi, e);
+    const DF s = two_sum(p, z.hi);
+    return DF{s.hi, __fadd_rn(s.lo, __fadd_rn(e, z.lo))};
+}
+
+__device__ __forceinline__ DF df_norm(DF x) {
+    return two_sum(x.hi, x.lo);
+}
+
 // Dot products sum_j c_j k_j of double-float terms, in the style of Ogita,
 // Rump & Oishi's Dot2: the high parts' products are accumulated exactly with
 // TwoSum, and their rounding errors, the products' own errors (by FMA) and the
@@ -222,36 +269,39 @@ __device__ __forceinline__ RayDF make_ray_df(const RayConst& R) {
 
 __device__ __forceinline__ void kerr_flow_df_body(const KerrDF& k, const RayDF& R, const StateDF& y, StateDF& f,
                                                   DF& H) {
+    // products of renormalised values in the lazy form (their lo stays within
+    // ~2 ulps of hi); every sum, which may cancel, renormalises, so that no
+    // cancelled value carries a large lo into a product
     DF s, c;
     df_sincos(y.th, s, c);
     const DF r = y.r;
-    const DF s2 = df_sqr(s), c2 = df_sqr(c), sc = df_mul(s, c);
-    const DF r2 = df_sqr(r);
+    const DF s2 = df_sqr_lazy(s), c2 = df_sqr_lazy(c), sc = df_mul_lazy(s, c);
+    const DF r2 = df_sqr_lazy(r);
     const DF Sig = df_fma(k.a2, c2, r2);
     const DF Del = df_fma(r, df_sub(r, k.twoM), k.a2);
     const DF A = df_fma(df_add(r2, k.a2), R.pt, R.apph);
-    const DF SD = df_mul(Sig, Del);
-    const DF inv = df_rcp(df_mul(SD, s2));
-    const DF iS = df_mul(inv, df_mul(Del, s2));
-    const DF iD = df_mul(inv, df_mul(Sig, s2));
-    const DF u = df_mul(inv, SD);
-    const DF pr2 = df_sqr(y.pr);
+    const DF SD = df_mul_lazy(Sig, Del);
+    const DF inv = df_rcp(df_norm(df_mul_lazy(SD, s2)));
+    const DF iS = df_mul_lazy(inv, df_mul_lazy(Del, s2));
+    const DF iD = df_mul_lazy(inv, df_mul_lazy(Sig, s2));
+    const DF u = df_mul_lazy(inv, SD);
+    const DF pr2 = df_sqr_lazy(y.pr);
     const DF AiD = df_mul(A, iD);
     DF K = df_fma(R.a2pt2, s2, R.c0);
     K = df_fma(R.pph2, u, K);
-    K = df_add(K, df_sqr(y.pth));
+    K = df_add(K, df_sqr_lazy(y.pth));
     K = df_fma(Del, pr2, K);
-    K = df_sub(K, df_mul(A, AiD));
+    K = df_sub(K, df_mul_lazy(A, AiD));
     const DF H2 = df_mul(K, iS);
     H = DF{0.5f * H2.hi, 0.5f * H2.lo};
     const DF q1 = df_fma(R.pt2, AiD, H2);
-    const DF q2 = df_add(df_sqr(AiD), pr2);
-    const DF t1 = df_sub(R.a2pt2, df_mul(R.pph2, df_sqr(u)));
+    const DF q2 = df_add(df_sqr_lazy(AiD), pr2);
+    const DF t1 = df_sub(R.a2pt2, df_mul_lazy(R.pph2, df_sqr_lazy(u)));
     const DF t2 = df_fma(k.a2, H2, t1);
-    f.r = df_mul(df_mul(Del, y.pr), iS);
+    f.r = df_mul(df_mul_lazy(Del, y.pr), iS);
     f.th = df_mul(y.pth, iS);
-    f.pr = df_mul(df_sub(df_mul(r, q1), df_mul(df_sub(r, k.M), q2)), iS);
-    f.pth = df_neg(df_mul(df_mul(sc, iS), t2));
+    f.pr = df_mul(df_sub(df_mul_lazy(r, q1), df_mul_lazy(df_sub(r, k.M), q2)), iS);
+    f.pth = df_neg(df_mul(df_mul_lazy(sc, iS), t2));
 }
 
 // One out-of-line copy, arguments and results by value (in registers).
@@ -328,23 +378,6 @@ __device__ __forceinline__ DF df_log(DF x) {
 // coefficients per cell and field, Horner's rule for the value and both
 // unit-cell derivatives) with double-float coefficients and arithmetic.
 // ---------------------------------------------------------------------------
-// x y + z without the closing renormalisation: lo may exceed half an ulp of hi
-// by a few bits, which the next multiply-add of a Horner chain absorbs (it takes
-// x.lo into an FP32 cross term, an error of ~2^-48 of the terms either way,
-// also where the sum cancels); chains are renormalised at their end.
-__device__ __forceinline__ DF df_fma_lazy(DF x, DF y, DF z) {
-    const float p = __fmul_rn(x.hi, y.hi);
-    float e = fmaf(x.hi, y.hi, -p);
-    e = fmaf(x.hi, y.lo, e);
-    e = fmaf(x.lo, y.hi, e);
-    const DF s = two_sum(p, z.hi);
-    return DF{s.hi, __fadd_rn(s.lo, __fadd_rn(e, z.lo))};
-}
-
-__device__ __forceinline__ DF df_norm(DF x) {
-    return two_sum(x.hi, x.lo);
-}
-
 // p = c0 + c1 x + c2 x^2 + c3 x^3 and dp = dp/dx (both left unnormalised)
 __device__ __forceinline__ void horner_d_df(DF c0, DF c1, DF c2, DF c3, DF x, DF& p, DF& dp) {
     DF q = df_fma_lazy(c3, x, c2);
