@@ -64,7 +64,7 @@ FP32_PEAK_TFLOPS = SM_COUNT * SM_MAX_MHZ * 1e6 * 128 * 2 / 1e12
 FP64_ISSUED_PER_STEP = (281.2, 208.6, 19.5)
 # FP32 thread instructions (FFMA + FMUL + FADD) per double-float step attempt, measured by ncu
 # on the 512^2 image (profiles/trace_kernel_df_kerr_disk_1024.md)
-DF_FP32_INST_PER_STEP = 5030
+DF_FP32_INST_PER_STEP = 4693
 BYTES_OUT_PER_PIXEL = 3 * 3 * 8 + 8 + 8 + 4 + 4 + 1 + 1
 # DRAM traffic of the FP64 tracer per ray: ncu's dram__bytes_read.sum + dram__bytes_write.sum of
 # the 512^2 capture (profiles/trace_kernel64_kerr_disk_1024.md) divided by its 262,144 rays
