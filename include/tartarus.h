@@ -289,6 +289,19 @@ int tartarus_table_create(const double *host_nodes, int nr, int nth, double r_mi
                           tt_table **out);
 int tartarus_table_destroy(tt_table *table);
 
+/* Host only (no GPU, no CUDA call): the per-cell patch coefficients that
+ * tartarus_table_create uploads, for the same arguments and with the same
+ * validation (TT_EINVAL on null pointers, nr or nth < 2, bad radii or a
+ * non-finite node value).  out (caller-owned) receives (nth - 1)(nr - 1) * 80
+ * doubles: cell (j, k) -- theta interval j, radial interval k -- at offset
+ * (j (nr - 1) + k) * 80, then per field f in the node order (g_tt, g_tphi,
+ * g_thth, g_phiphi, g^rr) 16 numbers c[4 i + q], the coefficients of t^i w^q
+ * in the field's bicubic Hermite patch, where t = (ln r - ln r_min)/du - k and
+ * w = theta/dth - j are the cell's unit coordinates (du = ln(r_max/r_min)/(nr-1),
+ * dth = pi/(nth-1)). */
+int tartarus_table_coefficients(const double *host_nodes, int nr, int nth, double r_min, double r_max,
+                                double *out);
+
 /* Static description of a status code. */
 const char *tartarus_error_string(int status);
 

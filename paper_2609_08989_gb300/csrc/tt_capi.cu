@@ -537,9 +537,9 @@ int tartarus_trace_batch(const tt_image* images, int n, const tt_solver* solver,
     return worst;
 }
 
-int tartarus_table_create(const double* host_nodes, int nr, int nth, double r_min, double r_max, tt_table** out) {
-    if (!out) return TT_EINVAL;
-    *out = nullptr;
+// The per-cell patch coefficients of a node table (validated), host only.
+static int table_coefficients(const double* host_nodes, int nr, int nth, double r_min, double r_max,
+                              std::vector<double>& cf) {
     if (!host_nodes || nr < 2 || nth < 2) return TT_EINVAL;
     if (!is_finite(r_min) || !is_finite(r_max) || !(r_min > 0.0) || !(r_max > r_min)) return TT_EINVAL;
     const size_t n = (size_t)nr * (size_t)nth * tt::kTableNF;
@@ -571,7 +571,7 @@ int tartarus_table_create(const double* host_nodes, int nr, int nth, double r_mi
     // with half the multiply-adds and no basis functions.
     static const double Hm[4][4] = {{1, 0, -3, 2}, {0, 1, -2, 1}, {0, 0, 3, -2}, {0, 0, -1, 1}};
     const size_t ncoef = (size_t)(nr - 1) * (size_t)(nth - 1) * tt::kTableCoef;
-    std::vector<double> cf(ncoef);
+    cf.assign(ncoef, 0.0);
     for (int j = 0; j + 1 < nth; ++j) {
         for (int k = 0; k + 1 < nr; ++k) {
             double* dst = cf.data() + ((size_t)j * (nr - 1) + k) * tt::kTableCoef;
@@ -602,6 +602,26 @@ int tartarus_table_create(const double* host_nodes, int nr, int nth, double r_mi
             }
         }
     }
+    return TT_OK;
+}
+
+int tartarus_table_coefficients(const double* host_nodes, int nr, int nth, double r_min, double r_max,
+                                double* out) {
+    if (!out) return TT_EINVAL;
+    std::vector<double> cf;
+    const int rc = table_coefficients(host_nodes, nr, nth, r_min, r_max, cf);
+    if (rc) return rc;
+    std::copy(cf.begin(), cf.end(), out);
+    return TT_OK;
+}
+
+int tartarus_table_create(const double* host_nodes, int nr, int nth, double r_min, double r_max, tt_table** out) {
+    if (!out) return TT_EINVAL;
+    *out = nullptr;
+    std::vector<double> cf;
+    const int rc = table_coefficients(host_nodes, nr, nth, r_min, r_max, cf);
+    if (rc) return rc;
+    const size_t ncoef = cf.size();
     // the double-float copy
     std::vector<float2> cdf(ncoef);
     for (size_t i = 0; i < ncoef; ++i) cdf[i] = split_df(cf[i]);

@@ -22,8 +22,8 @@ MAX_CROSSINGS = 3
 TABLE_NF = 20
 
 EXPORTS = ["tartarus_trace", "tartarus_trace_host", "tartarus_trace_batch", "tartarus_trace_batch_noalloc",
-           "tartarus_table_create",
-           "tartarus_table_destroy", "tartarus_error_string", "tartarus_launch_count", "tartarus_version"]
+           "tartarus_table_create", "tartarus_table_destroy", "tartarus_table_coefficients",
+           "tartarus_error_string", "tartarus_launch_count", "tartarus_version"]
 
 
 class TTMetric(C.Structure):
@@ -111,6 +111,9 @@ def lib():
             L.tartarus_table_create.restype = C.c_int
             L.tartarus_table_destroy.argtypes = [C.c_void_p]
             L.tartarus_table_destroy.restype = C.c_int
+            L.tartarus_table_coefficients.argtypes = [P(C.c_double), C.c_int, C.c_int, C.c_double, C.c_double,
+                                                      P(C.c_double)]
+            L.tartarus_table_coefficients.restype = C.c_int
             L.tartarus_error_string.argtypes = [C.c_int]
             L.tartarus_error_string.restype = C.c_char_p
             L.tartarus_launch_count.argtypes = []
@@ -136,6 +139,20 @@ def version() -> str:
 def _check(status: int, what: str):
     if status != TT_OK:
         raise TartarusError(status, what)
+
+
+def table_coefficients(nodes: np.ndarray, r_min: float, r_max: float) -> np.ndarray:
+    """tartarus_table_coefficients (host only): the per-cell patch coefficients,
+    shaped [nth - 1, nr - 1, 5, 4, 4] (cell j, k; field; power of t; power of w)."""
+    nodes = np.ascontiguousarray(nodes, dtype=np.float64)
+    if nodes.ndim != 3 or nodes.shape[2] != TABLE_NF:
+        raise ValueError("table nodes must have shape [nth, nr, 20]")
+    nth, nr = nodes.shape[0], nodes.shape[1]
+    out = np.empty((max(nth - 1, 0), max(nr - 1, 0), 5, 4, 4))
+    P = C.POINTER(C.c_double)
+    _check(lib().tartarus_table_coefficients(nodes.ctypes.data_as(P), nr, nth, float(r_min), float(r_max),
+                                             out.ctypes.data_as(P)), "tartarus_table_coefficients")
+    return out
 
 
 class Table:

@@ -2,10 +2,12 @@
 declares, its struct layouts match the binding, and argument validation
 rejects bad input before touching the GPU (no GPU needed)."""
 import ctypes as C
+import math
 import os
 import re
 import subprocess
 
+import numpy as np
 import pytest
 
 from paper_2609_08989_gb300 import _build, scenes, tartarus as T
@@ -138,3 +140,65 @@ def test_batch_mixing_metric_kinds_refused_for_one_kind_kernels():
         for fn in (T.lib().tartarus_trace_batch, T.lib().tartarus_trace_batch_noalloc):
             assert fn(imgs, 2, C.byref(s), None, status, None) == T.TT_EUNSUPPORTED
             assert list(status) == [-7, -7]          # refused before any image was looked at
+
+
+def test_table_coefficients_reproduce_the_oracle_interpolant(orc):
+    """The per-cell monomial coefficients the library uploads (formed on the
+    host from the Hermite node data) evaluate to the oracle's bicubic Hermite
+    interpolant: values of the five fields, and derivatives through the
+    oracle's inverse metric -- inside the table and beyond its radial range."""
+    a, nr, nth, rmax = 0.9, 40, 25, 200.0
+    rh = orc.rplus(1.0, a)
+    nodes = orc.kerr_table(1.0, a, nr, nth, rh, rmax)
+    cf = T.table_coefficients(nodes, rh, rmax)
+    assert cf.shape == (nth - 1, nr - 1, 5, 4, 4)
+    sc = scenes.Scene(metric_kind=1, a=a, table=nodes, r_min=rh, r_max=rmax)
+    u0 = math.log(rh)
+    du = (math.log(rmax) - u0) / (nr - 1)
+    dth = math.pi / (nth - 1)
+    rng = np.random.default_rng(17)
+    pts = [(rh * (rmax * 1.2 / rh) ** rng.uniform(0.02, 1.0), rng.uniform(0.05, math.pi - 0.05)) for _ in range(60)]
+    pts += [(rmax * 1.15, 1.0), (rh * 1.001, 2.0)]
+    ip = np.arange(4.0)
+    for r, th in pts:
+        tu, tw = (math.log(r) - u0) / du, th / dth
+        k, j = min(max(int(math.floor(tu)), 0), nr - 2), min(max(int(math.floor(tw)), 0), nth - 2)
+        t, w = tu - k, tw - j
+        T4, W4 = t ** ip, w ** ip
+        dT4 = np.array([0.0, 1.0, 2 * t, 3 * t * t])
+        dW4 = np.array([0.0, 1.0, 2 * w, 3 * w * w])
+        val = [T4 @ cf[j, k, f] @ W4 for f in range(5)]
+        dr = [dT4 @ cf[j, k, f] @ W4 / (du * r) for f in range(5)]
+        dt = [T4 @ cf[j, k, f] @ dW4 / dth for f in range(5)]
+        g = orc.metric_lower(sc, r, th)
+        gi, dgr, dgt = orc.metric_upper(sc, r, th)
+        for f, (mu, nu) in enumerate([(0, 0), (0, 3), (2, 2), (3, 3)]):
+            assert val[f] == pytest.approx(g[mu, nu], rel=1e-12, abs=1e-12 * abs(g[3, 3])), (r, th, f)
+        assert val[4] == pytest.approx(gi[1, 1], rel=1e-12), (r, th)
+        # derivatives: of g^rr directly, of g_thth through g^thth = 1/g_thth, of the
+        # (t, phi) block through g^tt = g_phiphi / D, D = g_tt g_phiphi - g_tphi^2
+        D = val[0] * val[3] - val[1] ** 2
+        for dv, dg in ((dr, dgr), (dt, dgt)):
+            assert dv[4] == pytest.approx(dg[1, 1], rel=1e-9, abs=1e-12)
+            assert -dv[2] / val[2] ** 2 == pytest.approx(dg[2, 2], rel=1e-9, abs=1e-14)
+            dD = dv[0] * val[3] + val[0] * dv[3] - 2 * val[1] * dv[1]
+            dgtt = (dv[3] * D - val[3] * dD) / D ** 2
+            assert dgtt == pytest.approx(dg[0, 0], rel=1e-8, abs=1e-12 * abs(gi[0, 0])), (r, th)
+
+
+def test_table_coefficients_validation():
+    L = T.lib()
+    P = C.POINTER(C.c_double)
+    out = np.zeros(80)
+    nodes = np.ones((2, 2, 20))
+    assert L.tartarus_table_coefficients(None, 2, 2, 1.0, 2.0, out.ctypes.data_as(P)) == T.TT_EINVAL
+    assert L.tartarus_table_coefficients(nodes.ctypes.data_as(P), 2, 2, 1.0, 2.0, None) == T.TT_EINVAL
+    assert L.tartarus_table_coefficients(nodes.ctypes.data_as(P), 1, 2, 1.0, 2.0, out.ctypes.data_as(P)) == T.TT_EINVAL
+    assert L.tartarus_table_coefficients(nodes.ctypes.data_as(P), 2, 2, 2.0, 1.0, out.ctypes.data_as(P)) == T.TT_EINVAL
+    nodes[1, 1, 7] = np.nan
+    assert L.tartarus_table_coefficients(nodes.ctypes.data_as(P), 2, 2, 1.0, 2.0, out.ctypes.data_as(P)) == T.TT_EINVAL
+    # a constant field: c_00 = the value, every other coefficient zero
+    nodes = np.zeros((2, 2, 20))
+    nodes[:, :, 0] = 2.5
+    assert L.tartarus_table_coefficients(nodes.ctypes.data_as(P), 2, 2, 1.0, 2.0, out.ctypes.data_as(P)) == T.TT_OK
+    assert out[0] == 2.5 and np.all(out[1:] == 0.0)
