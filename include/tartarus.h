@@ -258,7 +258,7 @@ int tartarus_trace_batch(const tt_image *images, int n, const tt_solver *solver,
  * this is an interface for embedding).  For callers that must not allocate
  * device memory once they are running -- for example an application that
  * reserves its whole GPU memory budget at start-up and hands out all buffers
- * itself, where a driver allocation from a library could exceed or fragment
+ * itself, where a CUDA allocation made by a library could exceed or fragment
  * that budget.  tartarus_trace and tartarus_trace_batch allocate a small
  * counter buffer on their first call on a device; this entry point instead
  * uses a fixed 4 KiB array of work-queue counters compiled into the library

@@ -302,7 +302,7 @@ unsigned long long* queue_slot() {
 
 // The device-side output block of tartarus_trace_host comes from the device's
 // default stream-ordered pool; keep freed blocks in the pool instead of
-// returning them to the driver at every synchronisation.
+// returning them to the CUDA runtime at every synchronisation.
 void keep_pool_memory() {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return;
