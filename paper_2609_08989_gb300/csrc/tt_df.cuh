@@ -362,7 +362,8 @@ __device__ __forceinline__ DF df_log(DF x) {
     const float w = q * fmaf(q, fmaf(q, 2.0f / 9.0f, 2.0f / 7.0f), 2.0f / 5.0f);
     constexpr DF TWO3 = df_const(2.0 / 3.0);
     const DF lm = df_add(DF{2.0f * sv.hi, 2.0f * sv.lo}, df_mul(df_mul(s2, sv), df_add_f(TWO3, w)));
-    // e ln 2 with ln 2 in three parts (the third keeps e ln 2 exact to ~2^-70 e)
+    // e ln 2 with ln 2 in three parts (hi and lo of the double-float and the
+    // float nearest the rest), so that it carries the double ln 2's ~1e-17
     constexpr double kLn2 = 0.69314718055994530942;
     constexpr DF L2 = df_const(kLn2);
     constexpr float L3 = (float)(kLn2 - (double)L2.hi - (double)L2.lo);
