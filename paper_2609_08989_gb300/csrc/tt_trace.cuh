@@ -568,6 +568,16 @@ template <int METRIC>
 __device__ bool init_ray(Lane& L, const ImageDesc* d_ptr, long long q, const SolverDesc& sol) {
     const ImageDesc& d = *d_ptr;
     L.d = d_ptr;
+    // A whole image whose sides are multiples of 8 and 4 is handed out in
+    // 8 x 4 pixel tiles (32 consecutive queue entries per tile), so that the
+    // rays a warp takes together start close on the sky and stay in step;
+    // q becomes the tile's pixel.  Outputs are per pixel either way.
+    if (d.pix_begin == 0 && d.pix_count == (long long)d.nx * d.ny && (d.nx & 7) == 0 && (d.ny & 3) == 0) {
+        const long long tile = q >> 5, tiles_x = d.nx >> 3;
+        const long long ty = tile / tiles_x, tx = tile - ty * tiles_x;
+        const int lane = (int)(q & 31);
+        q = (ty * 4 + (lane >> 3)) * d.nx + tx * 8 + (lane & 7);
+    }
     L.q = q;
     L.kk = make_kerr(d.M, d.a);
     L.steps = 0;
