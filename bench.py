@@ -68,7 +68,7 @@ DF_FP32_INST_PER_STEP = 4693
 BYTES_OUT_PER_PIXEL = 3 * 3 * 8 + 8 + 8 + 4 + 4 + 1 + 1
 # DRAM traffic of the FP64 tracer per ray: ncu's dram__bytes_read.sum + dram__bytes_write.sum of
 # the 512^2 capture (profiles/trace_kernel64_kerr_disk_1024.md) divided by its 262,144 rays
-TRAFFIC_BYTES_PER_RAY = (934144.0 + 0.0) / 262144.0
+TRAFFIC_BYTES_PER_RAY = (440320.0 + 0.0) / 262144.0
 # host-to-device input of one step: the image descriptor (sizeof(tt::ImageDesc)) and the queue reset
 DESC_BYTES = 384 + 8
 
