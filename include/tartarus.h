@@ -70,6 +70,8 @@ extern "C" {
 #define TT_MIXED         1   /* FP32 stages, FP64 state accumulation   */
 #define TT_MIXED_PAIR    2   /* FP32 stages, compensated FP32-pair state accumulation (~48 bits) */
 #define TT_DOUBLE_FLOAT  3   /* every stage in double-float (FP32 pairs, ~48 bits) on the FP32 pipe */
+#define TT_MIXED_SPLIT   4   /* FP32 stages; FP64 state accumulation, error norm and step control,
+                                FP64 steps near the horizon and FP64 crossing refinement */
 #define TT_REFINE_HENON   0  /* exact step onto theta = pi/2 (default) */
 #define TT_REFINE_HERMITE 1  /* paper's cubic-Hermite bisection        */
 #define TT_REFINE_HENON64 2  /* Henon with FP64 stages on the mixed paths too (default there: FP32 stages) */
@@ -104,25 +106,45 @@ typedef struct {
  * r < r_h (1 + horizon_eps), escaped when r > escape_factor * r_obs
  * (escape_factor > 1).  fp64_radius_factor (mixed paths, and the
  * double-float path on a table): steps that start at r < fp64_radius_factor *
- * r_h run in extended precision (0 selects 2, negative: none); so do steps that
- * start within asin(fp64_pole_sin) of the polar axis (0 selects 0.3 on the
- * mixed paths and none on a table, negative: none), where L^2 / sin^2(theta)
+ * r_h run in extended precision (0 selects 2, or 1.5 for TT_MIXED_SPLIT;
+ * negative: none); so do steps that start within asin(fp64_pole_sin) of the
+ * polar axis (0 selects 0.3 on TT_MIXED and TT_MIXED_PAIR and none on
+ * TT_MIXED_SPLIT and on a table, negative: none), where L^2 / sin^2(theta)
  * makes FP32 lose the constraint.  The defaults keep |H| <= 1e-6 on escaped
  * rays at rtol 1e-8.  TT_MIXED and TT_MIXED_PAIR run these extended-precision
- * steps in double-float (FP32-pair, ~48-bit) arithmetic on the FP32 pipe.
+ * steps in double-float (FP32-pair, ~48-bit) arithmetic on the FP32 pipe;
+ * TT_MIXED_SPLIT runs them in FP64, forms the error norm and the step-size
+ * control of its FP32 steps in FP64 from the FP32 error terms, and refines
+ * crossings with FP64 stages (the precision split stated for the mixed path,
+ * kept for comparison).
+ * critical_band, critical_rtol (mixed paths): a photon whose radial potential
+ * R(r) = r^4 + (a^2 - xi^2 - eta) r^2 + 2M (eta + (xi - a)^2) r - a^2 eta
+ * (xi = L/E, eta = Q/E^2, from its initial data) has a near-double root
+ * outside the horizon passes close to the unstable spherical photon orbits,
+ * and each circuit around them multiplies any perturbation of the ray by
+ * ~e^pi, so FP32 stage rounding (~1e-7) would reach its later crossings.
+ * A ray whose distance from the critical curve, estimated as
+ * R(r_m) / (2 r_m^2 b) at the local minimum r_m of R (b^2 = xi^2 + eta), is
+ * below critical_band (in units of M) is traced entirely in double-float, as
+ * TT_DOUBLE_FLOAT traces it, at rtol = atol = critical_rtol; these rays are
+ * traced first, by whole warps, in the same launch.  critical_band 0 selects
+ * 0.1 on TT_MIXED and TT_MIXED_PAIR and none on TT_MIXED_SPLIT, negative:
+ * none; critical_rtol 0 selects 1e-10.  Other precisions ignore both.
  * TT_DOUBLE_FLOAT steps every ray in double-float: flow, stage points, stage
  * sums and error estimate (with double-float coefficients) and the state, with
  * an FP32 error norm and step control; crossings are refined and emission
  * evaluated in FP64.  On a table its zone steps run in FP64, where the
  * interpolated D = g_tt g_phiphi - g_tphi^2 goes to zero at the horizon.
- * TT_MIXED and TT_MIXED_PAIR are available for the closed-form Kerr metric
- * (with a table they return TT_EUNSUPPORTED); TT_DOUBLE_FLOAT for either
+ * TT_MIXED, TT_MIXED_PAIR and TT_MIXED_SPLIT are available for the
+ * closed-form Kerr metric (with a table they return TT_EUNSUPPORTED);
+ * TT_DOUBLE_FLOAT for either
  * kind, but a batch that mixes both kinds returns TT_EUNSUPPORTED for it.
  * h_max is the largest |H| seen: on the FP64 path at the start and after every
  * accepted step; on the double-float path at the start (FP64) and after every
  * accepted step (double-float); on the mixed paths after every double-float
- * step, and in FP64 at the start of every step with a disk crossing, every
- * monitor_period warp iterations and at the end.
+ * or FP64 step, and in FP64 at the start of every step with a disk crossing,
+ * every monitor_period warp iterations and at the end (rays of the critical
+ * band as on the double-float path).
  * method: one of the five integrators of Sec. 3.2.  The embedded 5(4) pairs
  * (TT_DP54, TT_CK45, TT_F45) propagate their fifth-order solution and take the
  * difference to the fourth-order one as the error estimate.  TT_GBS: macro-
@@ -142,13 +164,15 @@ typedef struct {
  * TT_DP54 only. */
 typedef struct {
     int method;                 /* TT_DP54, TT_CK45, TT_F45, TT_GBS or TT_VERLET */
-    int precision;              /* TT_FP64, TT_MIXED, TT_MIXED_PAIR or TT_DOUBLE_FLOAT */
+    int precision;              /* TT_FP64, TT_MIXED, TT_MIXED_PAIR, TT_DOUBLE_FLOAT or TT_MIXED_SPLIT */
     double rtol, atol, h0, h_min;
     long long max_steps;
     double horizon_eps, escape_factor;
     int refine;                 /* TT_REFINE_HENON, TT_REFINE_HERMITE or TT_REFINE_HENON64 */
     double fp64_radius_factor;
     double fp64_pole_sin;
+    double critical_band;
+    double critical_rtol;
 } tt_solver;
 
 /* Thin disk in the equatorial plane (paper Sec. 2.3).  r_in <= 0 selects the
@@ -208,7 +232,11 @@ typedef struct {
  *   monitor_period  mixed paths: evaluate |H| in FP64 every this many warp
  *                   iterations (default 32)
  *   fp64_wait       mixed paths: lanes waiting for a zone step get one after at
- *                   most this many warp iterations (default 64) */
+ *                   most this many warp iterations (default 64)
+ *   crit_stride     mixed paths with a critical band: one warp in crit_stride
+ *                   starts by scanning for near-critical rays (default 1: all)
+ *   crit_refill     mixed paths: a warp tracing near-critical rays refills once
+ *                   this many lanes are free (1..32, default 32) */
 typedef struct {
     int block;
     int reg_variant;
@@ -218,6 +246,8 @@ typedef struct {
     int fp64_batch;
     int monitor_period;
     int fp64_wait;
+    int crit_stride;
+    int crit_refill;
 } tt_tune;
 
 /* Trace one camera (paper Sec. 3.1 execution flow, steps 1-6): every pixel of
@@ -273,7 +303,10 @@ int tartarus_trace_batch(const tt_image *images, int n, const tt_solver *solver,
  *   - every call shares the same counters and zeroes the ones it uses on its
  *     stream before each launch, so two calls whose work overlaps on the GPU
  *     (different streams, or different host threads) race on them: serialise
- *     such calls, e.g. by issuing them on one stream.
+ *     such calls, e.g. by issuing them on one stream;
+ *   - every image is validated, and status[] written, before the first launch;
+ *     a TT_ECUDA return means that a launch failed after the earlier chunks of
+ *     64 images were enqueued.
  * No cudaMalloc, cudaFree or other allocating routine is called. */
 int tartarus_trace_batch_noalloc(const tt_image *images, int n, const tt_solver *solver,
                                  const tt_tune *tune, int *status, void *cuda_stream);

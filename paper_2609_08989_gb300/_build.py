@@ -1,7 +1,9 @@
-"""Build the CUDA library libtartarus.so in-tree (nvcc, sm_103a only).
+"""Build the CUDA libraries in-tree (nvcc, sm_103a only): libtartarus.so (the
+tracer behind include/tartarus.h) and libtt_peaks.so (the FMA-chain probe of
+the FP64 and FP32 pipes that the benchmark's roofline divides by).
 
 The translation units are compiled in parallel and linked with the static CUDA
-runtime; the result lands in paper_2609_08989_gb300/_build/.
+runtime; the results land in paper_2609_08989_gb300/_build/.
 """
 from __future__ import annotations
 
@@ -15,7 +17,9 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 SO = os.path.join(BUILD, "libtartarus.so")
-SOURCES = ["tt_capi.cu", "tt_kernel64.cu", "tt_kernel_mixed.cu", "tt_kernel_ck.cu", "tt_kernel_f.cu",
+PEAKS_SRC = "tt_peaks.cu"
+PEAKS_SO = os.path.join(BUILD, "libtt_peaks.so")
+SOURCES = ["tt_capi.cu", "tt_kernel64.cu", "tt_kernel_mixed.cu", "tt_kernel_split.cu", "tt_kernel_ck.cu", "tt_kernel_f.cu",
            "tt_kernel_gbs.cu", "tt_kernel_verlet.cu", "tt_kernel_df.cu"]
 HEADERS = ["tt_internal.h", "tt_device.cuh", "tt_df.cuh", "tt_trace.cuh", "tt_kernel_rk.cuh", os.path.join("..", "..", "include", "tartarus.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -36,9 +40,32 @@ def _newest_input() -> float:
     return max(os.path.getmtime(f) for f in files)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile (if stale) and return the path of libtartarus.so."""
+def build_peaks(force: bool = False) -> str:
+    """Compile (if stale) and return the path of libtt_peaks.so."""
     os.makedirs(BUILD, exist_ok=True)
+    src = os.path.join(CSRC, PEAKS_SRC)
+    if not force and os.path.exists(PEAKS_SO) and os.path.getmtime(PEAKS_SO) >= os.path.getmtime(src):
+        return PEAKS_SO
+    tmp = PEAKS_SO + ".%d.tmp" % os.getpid()
+    cmd = [nvcc(), *ARCH, *FLAGS, "-shared", "-cudart", "static", src, "-o", tmp]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError("nvcc failed for %s:\n%s%s" % (PEAKS_SRC, r.stdout, r.stderr))
+    os.replace(tmp, PEAKS_SO)
+    return PEAKS_SO
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile (if stale) both libraries and return the path of libtartarus.so."""
+    os.makedirs(BUILD, exist_ok=True)
+    with ThreadPoolExecutor(1) as side:
+        peaks = side.submit(build_peaks, force)
+        so = _build_tracer(force, verbose)
+        peaks.result()
+    return so
+
+
+def _build_tracer(force: bool, verbose: bool) -> str:
     if not force and os.path.exists(SO) and os.path.getmtime(SO) >= _newest_input():
         return SO
     objs = []

@@ -10,7 +10,8 @@ built-in defaults, two sweeps), and keeps the winners per workload class in
 and ``trace_batch`` use the cached shape when no explicit ``tune`` is given.
 
 Workload classes: "fp64" (closed-form Kerr, FP64), "mixed" (FP32 stages with
-FP64 accumulation), "mixed_pair" (FP32-pair accumulation), "double_float"
+FP64 accumulation), "mixed_pair" (FP32-pair accumulation), "mixed_split" (the
+prescribed FP64 split), "double_float"
 (every step in double-float), "table" (FP64 on a tabulated metric),
 "table_double_float" (double-float on a tabulated metric).  Results are
 identical for every shape; only time changes.
@@ -36,6 +37,7 @@ SPACE: Dict[str, Dict[str, List[int]]] = {
               "fp64_wait": [64, 256, 1024], "monitor_period": [16, 32, 64], "blocks_per_sm": [0, 1, 2]},
 }
 SPACE["mixed_pair"] = SPACE["mixed"]
+SPACE["mixed_split"] = SPACE["mixed"]
 SPACE["double_float"] = {"refill": [2, 4, 8, 16, 32], "crossing_batch": [4, 8, 16, 32], "blocks_per_sm": [0, 1, 2]}
 SPACE["table_double_float"] = {"refill": [2, 4, 8, 16, 32], "crossing_batch": [4, 8, 16, 32], "fp64_batch": [1, 4, 16]}
 
@@ -43,7 +45,7 @@ SPACE["table_double_float"] = {"refill": [2, 4, 8, 16, 32], "crossing_batch": [4
 def workload_class(sc) -> str:
     if sc.metric_kind == 1:
         return "table_double_float" if sc.precision == 3 else "table"
-    return {0: "fp64", 1: "mixed", 2: "mixed_pair", 3: "double_float"}[sc.precision]
+    return {0: "fp64", 1: "mixed", 2: "mixed_pair", 3: "double_float", 4: "mixed_split"}[sc.precision]
 
 
 def _device_key() -> str:

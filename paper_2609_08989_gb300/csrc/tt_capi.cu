@@ -66,7 +66,7 @@ int check_solver(const tt_solver* s) {
     if (!s) return TT_EINVAL;
     if (s->method < TT_DP54 || s->method > TT_VERLET) return TT_EINVAL;
     if (s->precision != TT_FP64 && s->precision != TT_MIXED && s->precision != TT_MIXED_PAIR &&
-        s->precision != TT_DOUBLE_FLOAT)
+        s->precision != TT_DOUBLE_FLOAT && s->precision != TT_MIXED_SPLIT)
         return TT_EINVAL;
     if (s->method != TT_DP54 && s->precision != TT_FP64) return TT_EUNSUPPORTED;
     if (!is_finite(s->rtol) || !is_finite(s->atol) || !(s->rtol > 0.0) || !(s->atol > 0.0)) return TT_EINVAL;
@@ -78,8 +78,11 @@ int check_solver(const tt_solver* s) {
     if (s->refine != TT_REFINE_HENON && s->refine != TT_REFINE_HERMITE && s->refine != TT_REFINE_HENON64)
         return TT_EINVAL;
     if (!is_finite(s->fp64_radius_factor) || !is_finite(s->fp64_pole_sin)) return TT_EINVAL;
+    if (!is_finite(s->critical_band) || !is_finite(s->critical_rtol) || s->critical_rtol < 0.0) return TT_EINVAL;
     return TT_OK;
 }
+
+bool mixed_precision(int p) { return p == TT_MIXED || p == TT_MIXED_PAIR || p == TT_MIXED_SPLIT; }
 
 int check_outputs(const tt_outputs* o) {
     if (!o) return TT_EINVAL;
@@ -169,10 +172,15 @@ int make_desc(const tt_metric* m, const tt_observer* obs, const tt_camera* cam, 
     // escaped ray of the benchmark image and of the 64-image batch at rtol 1e-8.
     // Double-float path on a table: the same zones run in FP64 (pole default:
     // none -- the measured crossings and |H| do not change with it).
+    // The prescribed split (TT_MIXED_SPLIT): FP64 steps below 1.5 r_h, no pole zone.
     const bool df_table = m->kind == TT_METRIC_TABLE && sol->precision == TT_DOUBLE_FLOAT;
-    const double pole_default = df_table ? -1.0 : 0.3;
+    const bool split = sol->precision == TT_MIXED_SPLIT;
+    const double pole_default = (df_table || split) ? -1.0 : 0.3;
     const double pole_sin = sol->fp64_pole_sin != 0.0 ? sol->fp64_pole_sin : pole_default;
-    d->r_fp64 = sol->fp64_radius_factor < 0.0 ? 0.0 : (sol->fp64_radius_factor > 0.0 ? sol->fp64_radius_factor : 2.0) * r_h;
+    const double radius_default = split ? 1.5 : 2.0;
+    d->r_fp64 = sol->fp64_radius_factor < 0.0
+                    ? 0.0
+                    : (sol->fp64_radius_factor > 0.0 ? sol->fp64_radius_factor : radius_default) * r_h;
     d->th_pole = pole_sin < 0.0 ? 0.0 : std::asin(std::min(1.0, pole_sin));
     d->disk = disk->enabled ? 1 : 0;
     d->max_cross = disk->enabled ? disk->max_crossings : 0;
@@ -229,11 +237,21 @@ tt::SolverDesc make_solver(const tt_solver* s) {
     sd.refine = s->refine;
     sd.precision = s->precision;
     sd.method = s->method;
+    // near-critical rays in double-float: mixed paths only (default band 0.1 M,
+    // none on the prescribed split), at the FP64 path's tolerance by default
+    sd.crit_band = 0.0;
+    sd.crit_rtol = sd.crit_atol = 0.0;
+    if (mixed_precision(s->precision)) {
+        const double band_default = s->precision == TT_MIXED_SPLIT ? -1.0 : 0.1;
+        const double band = s->critical_band != 0.0 ? s->critical_band : band_default;
+        sd.crit_band = band > 0.0 ? band : 0.0;
+        sd.crit_rtol = sd.crit_atol = s->critical_rtol > 0.0 ? s->critical_rtol : 1e-10;
+    }
     return sd;
 }
 
 tt::LaunchShape make_shape(const tt_tune* t) {
-    tt::LaunchShape s{0, 0, 0, 0, 0, 0, 0, 0};       // zeros: the kernel's defaults
+    tt::LaunchShape s{0, 0, 0, 0, 0, 0, 0, 0, 0, 0};       // zeros: the kernel's defaults
     if (t) {
         if (t->block > 0) s.block = t->block;
         if (t->reg_variant > 0) s.reg_variant = t->reg_variant;
@@ -243,6 +261,8 @@ tt::LaunchShape make_shape(const tt_tune* t) {
         if (t->fp64_batch > 0) s.fp64_batch = t->fp64_batch;
         if (t->monitor_period > 0) s.monitor_period = t->monitor_period;
         if (t->fp64_wait > 0) s.fp64_wait = t->fp64_wait;
+        if (t->crit_stride > 0) s.crit_stride = t->crit_stride;
+        if (t->crit_refill > 0) s.crit_refill = t->crit_refill;
     }
     return s;
 }
@@ -259,6 +279,7 @@ int check_shape(const tt_tune* t) {
     if (t->crossing_batch < 0 || t->crossing_batch > 32) return TT_EINVAL;
     if (t->fp64_batch < 0 || t->fp64_batch > 32) return TT_EINVAL;
     if (t->monitor_period < 0 || t->fp64_wait < 0) return TT_EINVAL;
+    if (t->crit_stride < 0 || t->crit_refill < 0 || t->crit_refill > 32) return TT_EINVAL;
     return TT_OK;
 }
 
@@ -337,7 +358,7 @@ int enqueue(const std::vector<tt::ImageDesc>& descs, const tt_solver* sol, const
         const int metric_mode = n_table == 0 ? 0 : (n_table == (int)n ? 1 : 2);
         unsigned long long* q = queue_slot();
         if (!q) return TT_ENOMEM;
-        cudaError_t e = cudaMemsetAsync(q, 0, sizeof(unsigned long long), st);
+        cudaError_t e = cudaMemsetAsync(q, 0, 2 * sizeof(unsigned long long), st);
         if (e == cudaSuccess) e = tt::launch_trace(ds, (int)n, total, metric_mode, sd, shape, q, st);
         if (e != cudaSuccess) return TT_ECUDA;
         g_launches.fetch_add(1);
@@ -400,22 +421,25 @@ int tartarus_trace_batch_noalloc(const tt_image* images, int n, const tt_solver*
     const tt::SolverDesc sd = make_solver(solver);
     const tt::LaunchShape shape = make_shape(tune);
     int worst = TT_OK;
+    // every image is validated (and its status written) before the first launch
+    for (int i = 0; i < n; ++i) {
+        tt::ImageDesc d;
+        const tt_image& im = images[i];
+        const int r = make_desc(&im.metric, &im.obs, &im.cam, solver, &im.disk, &im.out, &d);
+        if (status) status[i] = r;
+        if (r) worst = r;
+    }
     int slot = 0;
     tt::ImageDesc ds[tt::kMaxImagesPerLaunch];
     int nd = 0;
     long long total = 0;
     int n_table = 0;
-    // validate and launch chunk by chunk (fixed-size host arrays, no heap)
+    // then the valid ones are launched chunk by chunk (fixed-size host arrays, no heap)
     for (int i = 0; i <= n; ++i) {
         if (i < n) {
             tt::ImageDesc d;
             const tt_image& im = images[i];
-            int r = make_desc(&im.metric, &im.obs, &im.cam, solver, &im.disk, &im.out, &d);
-            if (status) status[i] = r;
-            if (r) {
-                worst = r;
-                continue;
-            }
+            if (make_desc(&im.metric, &im.obs, &im.cam, solver, &im.disk, &im.out, &d)) continue;
             if (d.pix_count == 0) continue;
             d.ray_begin = total;
             total += d.pix_count;
@@ -426,8 +450,8 @@ int tartarus_trace_batch_noalloc(const tt_image* images, int n, const tt_solver*
             unsigned long long* q = scratch + (size_t)slot * 32;
             ++slot;
             const int metric_mode = n_table == 0 ? 0 : (n_table == nd ? 1 : 2);
-            // the array keeps the previous call's counts: zero this launch's counter first
-            cudaError_t e = cudaMemsetAsync(q, 0, sizeof(unsigned long long), st);
+            // the array keeps the previous call's counts: zero this launch's counters first
+            cudaError_t e = cudaMemsetAsync(q, 0, 2 * sizeof(unsigned long long), st);
             if (e == cudaSuccess) e = tt::launch_trace(ds, nd, total, metric_mode, sd, shape, q, st);
             if (e != cudaSuccess) return TT_ECUDA;
             g_launches.fetch_add(1);

@@ -68,8 +68,12 @@ struct SolverDesc {
     double rtol, atol, h0, h_min;
     long long max_steps;
     int refine;                   // 0 Henon, 1 Hermite, 2 Henon in FP64 on the mixed paths too
-    int precision;                // 0 FP64, 1 mixed (FP64 state), 2 mixed (FP32-pair state)
+    int precision;                // 0 FP64, 1 mixed (FP64 state), 2 mixed (FP32-pair state),
+                                  // 3 double-float, 4 mixed with the FP64 norm, zone steps and refinement
     int method;                   // 0 Dormand-Prince; FP64 only: 1 Cash-Karp, 2 Fehlberg, 3 GBS, 4 Verlet
+    // mixed paths: rays within crit_band (units of M) of the critical curve are
+    // traced in double-float at crit_rtol / crit_atol (0: none)
+    double crit_band, crit_rtol, crit_atol;
 };
 
 struct LaunchShape {
@@ -81,6 +85,8 @@ struct LaunchShape {
     int fp64_batch;
     int monitor_period;
     int fp64_wait;
+    int crit_stride;
+    int crit_refill;
 };
 
 // Warp-phase thresholds of the persistent loop (see tt_kernel.cu).
@@ -90,6 +96,8 @@ struct TuneParams {
     int fp64_batch;       // mixed: run the double-float zone steps once this many lanes need one
     int monitor_period;   // mixed: FP64 |H| check every this many iterations
     int fp64_wait;        // mixed: zone steps run after this many iterations of waiting
+    int crit_stride;      // mixed: one warp in crit_stride starts with the near-critical rays
+    int crit_refill;      // mixed: refill threshold of a warp tracing near-critical rays
 };
 
 // Images handed to one launch by value (kernel parameters, no host-to-device
@@ -99,10 +107,12 @@ constexpr int kMaxImagesPerLaunch = 64;
 template <int N>
 struct LaunchParams {
     SolverDesc sol;
+    SolverDesc solc;                 // mixed paths: the settings of the near-critical rays
     int n_desc;
     TuneParams tune;
     long long total;                 // rays over all images
-    unsigned long long* queue;       // zeroed 64-bit counter
+    unsigned long long* queue;       // two zeroed 64-bit counters: [0] the ray queue, [1] the
+                                     // mixed paths' scan for near-critical rays
     ImageDesc desc[N];
 };
 

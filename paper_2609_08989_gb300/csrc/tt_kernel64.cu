@@ -5,18 +5,18 @@ namespace tt {
 
 template <int METRIC, int N>
 __global__ void __launch_bounds__(128) trace_kernel64(const __grid_constant__ LaunchParams<N> p) {
-    trace_loop<METRIC, 0>(p.desc, p.n_desc, p.total, p.sol, p.tune, p.queue);
+    trace_loop<METRIC, 0>(p.desc, p.n_desc, p.total, p.sol, p.solc, p.tune, p.queue);
 }
 
 template <int METRIC, int N>
 __global__ void __launch_bounds__(256) trace_kernel64_b256(const __grid_constant__ LaunchParams<N> p) {
-    trace_loop<METRIC, 0>(p.desc, p.n_desc, p.total, p.sol, p.tune, p.queue);
+    trace_loop<METRIC, 0>(p.desc, p.n_desc, p.total, p.sol, p.solc, p.tune, p.queue);
 }
 
 // 384 threads (12 warps per SM at 160 registers, against 8 for 256 threads).
 template <int METRIC, int N>
 __global__ void __launch_bounds__(384) trace_kernel64_b384(const __grid_constant__ LaunchParams<N> p) {
-    trace_loop<METRIC, 0>(p.desc, p.n_desc, p.total, p.sol, p.tune, p.queue);
+    trace_loop<METRIC, 0>(p.desc, p.n_desc, p.total, p.sol, p.solc, p.tune, p.queue);
 }
 
 // Register-capped builds of the closed-form Kerr kernel (128 threads): at least
@@ -24,7 +24,7 @@ __global__ void __launch_bounds__(384) trace_kernel64_b384(const __grid_constant
 // (MINB 3: 168, MINB 4: 128).
 template <int MINB>
 __global__ void __launch_bounds__(128, MINB) trace_kernel64_regcap(const __grid_constant__ LaunchParams<1> p) {
-    trace_loop<0, 0>(p.desc, p.n_desc, p.total, p.sol, p.tune, p.queue);
+    trace_loop<0, 0>(p.desc, p.n_desc, p.total, p.sol, p.solc, p.tune, p.queue);
 }
 
 int sm_count() {

@@ -10,7 +10,7 @@ namespace tt {
 // spills and measured 10 % slower).
 template <int METRIC, int N>
 __global__ void __launch_bounds__(256) trace_kernel_df(const __grid_constant__ LaunchParams<N> p) {
-    trace_loop<METRIC, 3>(p.desc, p.n_desc, p.total, p.sol, p.tune, p.queue);
+    trace_loop<METRIC, 3>(p.desc, p.n_desc, p.total, p.sol, p.solc, p.tune, p.queue);
 }
 
 template <int METRIC, int N>

@@ -12,7 +12,7 @@ namespace tt {
 
 template <int METHOD, int METRIC, int N, int BLOCK>
 __global__ void __launch_bounds__(BLOCK) trace_kernel_rk(const __grid_constant__ LaunchParams<N> p) {
-    trace_loop<METRIC, 0, METHOD>(p.desc, p.n_desc, p.total, p.sol, p.tune, p.queue);
+    trace_loop<METRIC, 0, METHOD>(p.desc, p.n_desc, p.total, p.sol, p.solc, p.tune, p.queue);
 }
 
 template <int METHOD, int N>

@@ -505,6 +505,8 @@ struct Lane {
     float hmaxf;
     KerrDF kdf;
     RayDF rdf;
+    // mixed paths: a near-critical ray, traced in double-float
+    bool crit;
 };
 
 __device__ __forceinline__ void write_final(const Lane& L, int code) {
@@ -562,22 +564,79 @@ static __device__ float initial_step32(const Lane& L, const StateF& y0, float dr
     return fminf(100.0f * h0, h1);
 }
 
-// Initial data from the ZAMO tetrad (paper Sec. 2.2), time-reversed. Returns
-// false (and writes a BADPIXEL record) if the pixel is outside the sky.
-template <int METRIC>
-__device__ bool init_ray(Lane& L, const ImageDesc* d_ptr, long long q, const SolverDesc& sol) {
-    const ImageDesc& d = *d_ptr;
-    L.d = d_ptr;
-    // A whole image whose sides are multiples of 8 and 4 is handed out in
-    // 8 x 4 pixel tiles (32 consecutive queue entries per tile), so that the
-    // rays a warp takes together start close on the sky and stay in step;
-    // q becomes the tile's pixel.  Outputs are per pixel either way.
+// A whole image whose sides are multiples of 8 and 4 is handed out in 8 x 4
+// pixel tiles (32 consecutive queue entries per tile), so that the rays a warp
+// takes together start close on the sky and stay in step: the queue entry q of
+// such an image traces the tile's pixel returned here.  Outputs are per pixel
+// either way.
+__device__ __forceinline__ long long tile_pixel(const ImageDesc& d, long long q) {
     if (d.pix_begin == 0 && d.pix_count == (long long)d.nx * d.ny && (d.nx & 7) == 0 && (d.ny & 3) == 0) {
         const long long tile = q >> 5, tiles_x = d.nx >> 3;
         const long long ty = tile / tiles_x, tx = tile - ty * tiles_x;
         const int lane = (int)(q & 31);
         q = (ty * 4 + (lane >> 3)) * d.nx + tx * 8 + (lane & 7);
     }
+    return q;
+}
+
+// ---------------------------------------------------------------------------
+// Near-critical rays (mixed paths, closed-form Kerr).  With the photon's
+// constants of motion xi = L/E and eta = Q/E^2 (Q Carter's constant) the
+// radial motion obeys (Sigma dr/dlambda)^2 = E^2 R(r),
+//   R(r) = r^4 + (a^2 - xi^2 - eta) r^2 + 2 M (eta + (xi - a)^2) r - a^2 eta.
+// A ray on the critical curve (the shadow's edge) has a double root of R at a
+// spherical photon orbit r_m; a nearby ray lingers there for ~ln(1/delta)
+// circuits, each multiplying a perturbation by ~e^pi.  r_m is taken as the
+// largest root of R'(r) / 4 = r^3 + P r + C, P = (a^2 - xi^2 - eta)/2,
+// C = M (eta + (xi - a)^2)/2 (the local minimum of R; trigonometric form of
+// the cubic's three real roots), and R(r_m) / (2 r_m^2 b), b^2 = xi^2 + eta,
+// estimates the ray's distance from the critical curve in impact parameter
+// (dR/db = -2 b r^2 when xi and eta scale together).  Evaluated in FP32 (the
+// band, ~0.1 M, is ~10^6 times its rounding) from the observer's tetrad as in
+// init_ray; the same code classifies a ray in the scan and in the main pass,
+// so every ray is traced exactly once.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool near_critical(const ImageDesc& d, long long q, float band) {
+    const long long p = d.pix_begin + q;
+    const long long i = p % d.nx, j = p / d.nx;
+    const float al = (float)d.alpha_min + ((float)i + 0.5f) * (float)d.dalpha;
+    const float be = (float)d.beta_min + ((float)j + 0.5f) * (float)d.dbeta;
+    const float D = (float)d.r_obs;
+    if (!isfinite(al) || !isfinite(be) || !(fmaf(al, al, be * be) < D * D)) return false;
+    // physical momentum at the observer (ZAMO tetrad, as in init_ray)
+    const float iN = (float)d.obs_iN, omN = (float)d.obs_omN;
+    const float pu_th = (be / D) * (float)d.obs_ith;
+    const float pu_ph = fmaf(-al / D, (float)d.obs_iph, omN);
+    const float gtt = (float)d.obs_g[0], gtp = (float)d.obs_g[1], gthth = (float)d.obs_g[3], gpp = (float)d.obs_g[4];
+    const float E = -fmaf(gtt, iN, gtp * pu_ph);
+    const float Lz = fmaf(gtp, iN, gpp * pu_ph);
+    const float pth = gthth * pu_th;
+    float so, co;
+    sincosf((float)d.theta_obs, &so, &co);
+    const float a = (float)d.a, M = (float)d.M, a2 = a * a;
+    const float Q = fmaf(pth, pth, co * co * (Lz * Lz / (so * so) - a2 * E * E));
+    const float xi = Lz / E, eta = Q / (E * E);
+    const float P = 0.5f * (a2 - xi * xi - eta);
+    const float C = 0.5f * M * (eta + (xi - a) * (xi - a));
+    if (!(P < 0.0f) || !(4.0f * P * P * P + 27.0f * C * C < 0.0f)) return false;     // one real root: no minimum
+    const float m = 2.0f * sqrtf(-P * (1.0f / 3.0f));
+    const float cs = fminf(1.0f, fmaxf(-1.0f, 3.0f * C / (P * m)));
+    const float rm = m * cosf(acosf(cs) * (1.0f / 3.0f));
+    if (!(rm > (float)d.r_plus)) return false;
+    const float R = fmaf(fmaf(fmaf(rm, rm, 2.0f * P), rm, 4.0f * C), rm, -a2 * eta);
+    const float b = sqrtf(fmaxf(fmaf(xi, xi, eta), 1e-12f));
+    return fabsf(R) < band * M * (2.0f * rm * rm * b);
+}
+
+// Initial data from the ZAMO tetrad (paper Sec. 2.2), time-reversed, for the
+// pixel q (after tile_pixel).  Returns false (and writes a BADPIXEL record) if
+// the pixel is outside the sky.  df_init: set the ray up for double-float steps
+// (the double-float path, and near-critical rays of the mixed paths).
+template <int METRIC>
+__device__ bool init_ray(Lane& L, const ImageDesc* d_ptr, long long q, const SolverDesc& sol,
+                         bool df_init = false) {
+    const ImageDesc& d = *d_ptr;
+    L.d = d_ptr;
     L.q = q;
     L.kk = make_kerr(d.M, d.a);
     L.steps = 0;
@@ -637,7 +696,7 @@ __device__ bool init_ray(Lane& L, const ImageDesc* d_ptr, long long q, const Sol
     L.k32_ok = false;
     L.kdf_ok = false;
     L.hmaxf = 0.0f;
-    if (sol.precision == 0) {
+    if (sol.precision == 0 && !df_init) {
         double H0;
         flow64<METRIC>(d, L.kk, L.R, L.y, L.k1, H0);
         sincos(L.y.th, &L.s0, &L.c0);
@@ -658,8 +717,8 @@ __device__ bool init_ray(Lane& L, const ImageDesc* d_ptr, long long q, const Sol
         L.fp64f = (float)d.r_fp64;
         L.thpf = (float)d.th_pole;
         L.lamf = 0.0f;
-        if (sol.precision == 3) {
-            // double-float path: the FP64 path's starting step (once per ray), so
+        if (sol.precision == 3 || df_init) {
+            // double-float steps: the FP64 path's starting step (once per ray), so
             // that both begin the same step sequence
             L.kdf = make_kerr_df(L.kk);
             L.rdf = make_ray_df(L.R);
@@ -882,12 +941,14 @@ __device__ int step_ray64(Lane& L, const SolverDesc& sol) {
 }
 
 // ---------------------------------------------------------------------------
-// Mixed precision (closed-form Kerr).  The seven stages, the flow, the error
-// estimate and norm and the step-size control run in FP32.  The state is
-// accumulated either in FP64 (ACC 0: y_new = y + (double)(h sum b_i k_i)) or as
-// a compensated FP32 pair (ACC 1: hi + lo with TwoSum, ~48 bits), which needs
-// no FP64 instruction in the step.  Steps that start below r_fp64 run in FP64;
-// crossings are refined in FP64.
+// Mixed precision (closed-form Kerr).  The seven stages, the flow and the error
+// estimate run in FP32.  PREC 1 and 2: the error norm and the step-size control
+// in FP32 too; the state accumulated in FP64 (PREC 1: y_new = y + (double)(h
+// sum b_i k_i)) or as a compensated FP32 pair (PREC 2: hi + lo with TwoSum,
+// ~48 bits), which needs no FP64 instruction in the step.  PREC 4 (the
+// prescribed split): FP64 state, and the error norm and step control in FP64
+// from the FP32 error terms.  Steps in the zones near the horizon and the axis
+// are taken by the caller (double-float, or FP64 for PREC 4).
 // ---------------------------------------------------------------------------
 
 // hi + lo <- hi + lo + x (Knuth's TwoSum, then renormalised).
@@ -905,9 +966,9 @@ __device__ __forceinline__ bool pair_below(float hi, float lo, float ch, float c
     return ((hi - ch) + (lo - cl)) < 0.0f;
 }
 
-template <int ACC>
+template <int PREC>
 __device__ int step_ray32(Lane& L, StateF& yhi, const SolverDesc& sol) {
-    constexpr int PREC = ACC + 1;
+    constexpr int ACC = (PREC == 2) ? 1 : 0;
     const ImageDesc& d = *L.d;
     if ((long long)L.steps + (long long)L.rejects >= sol.max_steps) return 2;
     const float h = L.hf;
@@ -960,12 +1021,24 @@ __device__ int step_ray32(Lane& L, StateF& yhi, const SolverDesc& sol) {
 #define TT_E(f) \
     h * fmaf((float)e7, k7.f, fmaf((float)e6, k6.f, fmaf((float)e5, k5.f, fmaf((float)e4, k4.f, \
              fmaf((float)e3, k3.f, (float)e1 * k1.f)))))
-    const float atol = (float)sol.atol, rtol = (float)sol.rtol;
-    float err2 = sq_ratio32(TT_E(r), y.r, yn.r, atol, rtol);
-    err2 += sq_ratio32(TT_E(th), y.th, yn.th, atol, rtol);
-    err2 += sq_ratio32(TT_E(pr), y.pr, yn.pr, atol, rtol);
-    err2 += sq_ratio32(TT_E(pth), y.pth, yn.pth, atol, rtol);
-    err2 *= 0.25f;
+    float err2;
+    double err64 = 0.0;
+    State y64n;
+    if constexpr (PREC == 4) {
+        // FP64 norm from the FP32 error terms and the FP64 states
+        y64n = State{L.y.r + (double)inc.r, L.y.th + (double)inc.th, L.y.pr + (double)inc.pr,
+                     L.y.pth + (double)inc.pth};
+        const State e64 = State{(double)TT_E(r), (double)TT_E(th), (double)TT_E(pr), (double)TT_E(pth)};
+        err64 = err_norm2(L.y, y64n, e64, sol.atol, sol.rtol);
+        err2 = nan_bits(err64) ? __int_as_float(0x7fffffff) : (err64 <= 1.0 ? 0.0f : 2.0f);
+    } else {
+        const float atol = (float)sol.atol, rtol = (float)sol.rtol;
+        err2 = sq_ratio32(TT_E(r), y.r, yn.r, atol, rtol);
+        err2 += sq_ratio32(TT_E(th), y.th, yn.th, atol, rtol);
+        err2 += sq_ratio32(TT_E(pr), y.pr, yn.pr, atol, rtol);
+        err2 += sq_ratio32(TT_E(pth), y.pth, yn.pth, atol, rtol);
+        err2 *= 0.25f;
+    }
 #undef TT_E
 #undef TT_FS
 #undef TT_C2
@@ -979,11 +1052,12 @@ __device__ int step_ray32(Lane& L, StateF& yhi, const SolverDesc& sol) {
         L.steps++;
         bool captured, escaped;
         if (ACC == 0) {
-            State y64n;
-            y64n.r = L.y.r + (double)inc.r;
-            y64n.th = L.y.th + (double)inc.th;
-            y64n.pr = L.y.pr + (double)inc.pr;
-            y64n.pth = L.y.pth + (double)inc.pth;
+            if constexpr (PREC != 4) {
+                y64n.r = L.y.r + (double)inc.r;
+                y64n.th = L.y.th + (double)inc.th;
+                y64n.pr = L.y.pr + (double)inc.pr;
+                y64n.pth = L.y.pth + (double)inc.pth;
+            }
             if (d.disk && ((L.y.th <= kHalfPi) != (y64n.th <= kHalfPi))) note_crossing<0, PREC>(L, L.y, sol);
             L.y = y64n;
             captured = y64n.r < d.r_capture;
@@ -1010,16 +1084,42 @@ __device__ int step_ray32(Lane& L, StateF& yhi, const SolverDesc& sol) {
         L.kdf_ok = false;
         if (captured) return 1;
         if (escaped) return 0;
-        float fac = (err2 < 1e-30f) ? 10.0f : 0.9f * __powf(err2, -0.1f);
-        fac = fminf(L.last_rej ? 1.0f : 10.0f, fmaxf(0.2f, fac));
-        L.hf = h * fac;
+        if constexpr (PREC == 4) {
+            L.hf = (float)((double)h * fmin(L.last_rej ? 1.0 : 10.0, fmax(0.2, step_factor(err64))));
+        } else {
+            float fac = (err2 < 1e-30f) ? 10.0f : 0.9f * __powf(err2, -0.1f);
+            fac = fminf(L.last_rej ? 1.0f : 10.0f, fmaxf(0.2f, fac));
+            L.hf = h * fac;
+        }
         L.last_rej = false;
     } else {
         L.rejects++;
-        L.hf = h * fmaxf(0.2f, 0.9f * __powf(err2, -0.1f));
+        if constexpr (PREC == 4) L.hf = (float)((double)h * fmax(0.2, step_factor(err64)));
+        else L.hf = h * fmaxf(0.2f, 0.9f * __powf(err2, -0.1f));
         L.last_rej = true;
     }
     return -1;
+}
+
+// A zone step of the prescribed split (PREC 4): the FP64 Dormand-Prince step
+// from the FP64 state, with the FSAL flow, sin and cos taken afresh after FP32
+// steps; the step size and affine parameter are carried over from and back to
+// the FP32 steps.
+__device__ __forceinline__ int step_zone64_split(Lane& L, const SolverDesc& sol) {
+    if (!L.k64_ok) {
+        double H;
+        flow64<0>(*L.d, L.kk, L.R, L.y, L.k1, H);
+        sincos(L.y.th, &L.s0, &L.c0);
+        L.k64_ok = true;
+    }
+    L.h = (double)L.hf;
+    L.lam = (double)L.lamf;
+    const int code = step_ray64<0, 4>(L, sol);
+    L.hf = (float)L.h;
+    L.lamf = (float)L.lam;
+    L.k32_ok = false;
+    L.kdf_ok = false;
+    return code;
 }
 
 // ---------------------------------------------------------------------------
@@ -1259,15 +1359,26 @@ __device__ __forceinline__ int find_image(const ImageDesc* descs, int n, long lo
 // Lane states of the warp loop.
 enum : int { kIdle = 0, kRun = 1, kDone = 2 };
 
+
 // PREC 0: FP64.  PREC 1: mixed with FP64 accumulation.  PREC 2: mixed with the
-// compensated FP32-pair accumulation.  METHOD (FP64 only): 0 Dormand-Prince,
-// 1 Cash-Karp, 2 Fehlberg, 3 Gragg-Bulirsch-Stoer, 4 Verlet.
+// compensated FP32-pair accumulation.  PREC 3: double-float.  PREC 4: mixed
+// with the prescribed FP64 split (norm, zone steps, refinement).  METHOD (FP64
+// only): 0 Dormand-Prince, 1 Cash-Karp, 2 Fehlberg, 3 Gragg-Bulirsch-Stoer,
+// 4 Verlet.  solc: the solver settings of the mixed paths' near-critical rays.
+//
+// Mixed paths with a critical band: one warp in crit_stride scans the rays
+// (queue[1]) for near-critical ones and traces those in double-float, with
+// whole warps of them; the other warps take the rays from queue[0], skipping
+// the near-critical ones (the same test picks them out).  A warp whose queue
+// is drained takes the other one.  The long double-float rays thus start first
+// and overlap with the bulk of the image.
 template <int METRIC, int PREC, int METHOD = 0>
 __device__ __forceinline__ void trace_loop(const ImageDesc* descs, int n_desc, long long total,
-                                           const SolverDesc& sol, const TuneParams& tp,
+                                           const SolverDesc& sol, const SolverDesc& solc, const TuneParams& tp,
                                            unsigned long long* queue) {
     static_assert(PREC == 0 || METHOD == 0, "the mixed and double-float paths step with Dormand-Prince");
-    constexpr int ACC = (PREC >= 2) ? 1 : 0;
+    constexpr int ACC = (PREC == 2 || PREC == 3) ? 1 : 0;
+    constexpr bool MIX = (PREC == 1 || PREC == 2 || PREC == 4);
     if constexpr (PREC != 0) {
         df_sincos_table(s_df_tab);
         if constexpr (METRIC == 1) df_log_table(s_df_ln);
@@ -1276,23 +1387,69 @@ __device__ __forceinline__ void trace_loop(const ImageDesc* descs, int n_desc, l
     const int lane = threadIdx.x & 31;
     Lane L;
     L.pend = false;
+    L.crit = false;
     StateF yhi = {0.0f, 0.0f, 0.0f, 0.0f};   // pair accumulator: hi parts
     int st = kIdle;
     bool drained = false;
+    // one warp in crit_stride starts with the scan for near-critical rays, the
+    // others with the bulk; a warp whose queue is drained and whose lanes are
+    // all written takes the other queue, until both are drained (warp-uniform)
+    const float band = (float)sol.crit_band;
+    const bool use_crit = MIX && band > 0.0f;
+    bool crit_phase = use_crit && ((((blockIdx.x * blockDim.x + threadIdx.x) >> 5) % tp.crit_stride) == 0);
+    bool drained_c = !use_crit;
     int wait64 = 0;
     unsigned iter = 0;
+    // crossings of near-critical rays are refined as on the double-float path
+    auto refine = [&]() {
+        if constexpr (MIX) {
+            if (L.crit) {
+                refine_pending<METRIC, 3>(L, solc);
+                return;
+            }
+        }
+        refine_pending<METRIC, PREC, METHOD>(L, sol);
+    };
     for (;;) {
         // ---- refill phase: flush finished rays, start new ones -------------
+        // (near-critical rays differ widely in length: their warps refill at a
+        // threshold of their own)
         const int n_free = __popc(__ballot_sync(kFull, st != kRun));
-        if (n_free > 0 && (n_free >= tp.refill || n_free == 32) &&
-            (!drained || __any_sync(kFull, st == kDone))) {
-            if (st != kIdle && L.pend) refine_pending<METRIC, PREC, METHOD>(L, sol);
+        const bool more = crit_phase ? !drained_c : !drained;
+        const int refill_at = crit_phase ? tp.crit_refill : tp.refill;
+        if (n_free > 0 && (n_free >= refill_at || n_free == 32) && (more || __any_sync(kFull, st == kDone))) {
+            if (st != kIdle && L.pend) refine();
             if (st == kDone) {
-                if (PREC == 1 || PREC == 2) check_h64<ACC>(L, yhi);
+                if (MIX && !L.crit) check_h64<ACC>(L, yhi);
                 write_final(L, L.code);
                 st = kIdle;
             }
-            if (!drained) {
+            if (crit_phase) {
+                // fill the idle lanes with near-critical rays: each round tests one
+                // queue entry per idle lane (bounded: every round consumes entries)
+                while (!drained_c) {
+                    const unsigned idle = __ballot_sync(kFull, st == kIdle);
+                    if (!idle) break;
+                    const int n_idle = __popc(idle);
+                    unsigned long long base = 0;
+                    if (lane == 0) base = atomicAdd(queue + 1, (unsigned long long)n_idle);
+                    base = __shfl_sync(kFull, base, 0);
+                    if (base + (unsigned long long)n_idle >= (unsigned long long)total) drained_c = true;
+                    if (st == kIdle) {
+                        const long long rid = (long long)base + __popc(idle & ((1u << lane) - 1u));
+                        if (rid < total) {
+                            const int im = (n_desc == 1) ? 0 : find_image(descs, n_desc, rid);
+                            const ImageDesc* dp = descs + im;
+                            const long long q = tile_pixel(*dp, rid - dp->ray_begin);
+                            if (near_critical(*dp, q, band) && init_ray<METRIC>(L, dp, q, solc, true)) {
+                                st = kRun;
+                                L.crit = true;
+                                if (ACC == 1) split_state(L.y, yhi, L.lo);
+                            }
+                        }
+                    }
+                }
+            } else if (!drained) {
                 const unsigned idle = __ballot_sync(kFull, st == kIdle);
                 const int n_idle = __popc(idle);
                 unsigned long long base = 0;
@@ -1303,8 +1460,13 @@ __device__ __forceinline__ void trace_loop(const ImageDesc* descs, int n_desc, l
                     const long long rid = (long long)base + __popc(idle & ((1u << lane) - 1u));
                     if (rid < total) {
                         const int im = (n_desc == 1) ? 0 : find_image(descs, n_desc, rid);
-                        if (init_ray<METRIC>(L, descs + im, rid - descs[im].ray_begin, sol)) {
+                        const ImageDesc* dp = descs + im;
+                        const long long q = tile_pixel(*dp, rid - dp->ray_begin);
+                        // near-critical rays were traced in the scan
+                        const bool skip = MIX && band > 0.0f && near_critical(*dp, q, band);
+                        if (!skip && init_ray<METRIC>(L, dp, q, sol)) {
                             st = kRun;
+                            L.crit = false;
                             if (ACC == 1) split_state(L.y, yhi, L.lo);
                         }
                     }
@@ -1313,7 +1475,10 @@ __device__ __forceinline__ void trace_loop(const ImageDesc* descs, int n_desc, l
         }
         const unsigned running = __ballot_sync(kFull, st == kRun);
         if (!running) {
-            if (drained && !__any_sync(kFull, st == kDone)) break;
+            if (__any_sync(kFull, st == kDone)) continue;          // written by the next refill
+            // every lane idle: once this queue is drained, take the other one
+            if (drained && drained_c) break;
+            if (crit_phase ? drained_c : drained) crit_phase = !crit_phase;
             continue;
         }
         ++iter;
@@ -1358,13 +1523,22 @@ __device__ __forceinline__ void trace_loop(const ImageDesc* descs, int n_desc, l
                     st = kDone;
                 }
             }
+        } else if (crit_phase) {
+            // near-critical rays: every step in double-float, as on the double-float path
+            if (st == kRun) {
+                const int code = step_ray_df<METRIC, ACC, true>(L, yhi, solc);
+                if (code >= 0) {
+                    L.code = code;
+                    st = kDone;
+                }
+            }
         } else {
             bool want64 = false;
             if (st == kRun) {
-                // double-float near the horizon and near the axis (the coordinate
-                // singularities); the distance to the axis is |theta - m pi| for the
-                // nearest integer m, since a ray through the axis continues with
-                // theta outside (0, pi)
+                // extended precision near the horizon and near the axis (the
+                // coordinate singularities); the distance to the axis is
+                // |theta - m pi| for the nearest integer m, since a ray through the
+                // axis continues with theta outside (0, pi)
                 const float thf = (ACC == 0) ? (float)L.y.th : yhi.th;
                 const float rf = (ACC == 0) ? (float)L.y.r : yhi.r;
                 const float axis = fabsf(fmaf(-rintf(thf * 0.318309886f), 3.14159274f, thf));
@@ -1375,8 +1549,11 @@ __device__ __forceinline__ void trace_loop(const ImageDesc* descs, int n_desc, l
                 const bool run64 = (__popc(w64) >= tp.fp64_batch) || (w64 == running) || (wait64 >= tp.fp64_wait);
                 wait64 = run64 ? 0 : wait64 + 1;
                 if (run64 && want64) {
-                    // the extended-precision step, in double-float on the FP32 pipe
-                    const int code = step_ray_df<METRIC, ACC, false>(L, yhi, sol);
+                    // the zone step: FP64 on the prescribed split, else double-float on
+                    // the FP32 pipe
+                    int code;
+                    if constexpr (PREC == 4) code = step_zone64_split(L, sol);
+                    else code = step_ray_df<METRIC, ACC, false>(L, yhi, sol);
                     if (code >= 0) {
                         L.code = code;
                         st = kDone;
@@ -1384,7 +1561,7 @@ __device__ __forceinline__ void trace_loop(const ImageDesc* descs, int n_desc, l
                 }
             }
             if (st == kRun && !want64) {
-                const int code = step_ray32<ACC>(L, yhi, sol);
+                const int code = step_ray32<PREC>(L, yhi, sol);
                 if (code >= 0) {
                     L.code = code;
                     st = kDone;
@@ -1394,11 +1571,11 @@ __device__ __forceinline__ void trace_loop(const ImageDesc* descs, int n_desc, l
         // ---- batched crossing refinement -----------------------------------
         const unsigned pend = __ballot_sync(kFull, st == kRun && L.pend);
         if (pend && __popc(pend) >= tp.crossing_batch) {
-            if (st == kRun && L.pend) refine_pending<METRIC, PREC, METHOD>(L, sol);
+            if (st == kRun && L.pend) refine();
         }
         // ---- FP64 |H| monitor (mixed) --------------------------------------
-        if ((PREC == 1 || PREC == 2) && (iter % (unsigned)tp.monitor_period) == 0) {
-            if (st == kRun) check_h64<ACC>(L, yhi);
+        if (MIX && (iter % (unsigned)tp.monitor_period) == 0) {
+            if (st == kRun && !L.crit) check_h64<ACC>(L, yhi);
         }
     }
 }
@@ -1428,6 +1605,9 @@ template <int N>
 void fill_params(LaunchParams<N>& p, const ImageDesc* descs, int n, long long total, const SolverDesc& sol,
                  const LaunchShape& shape, unsigned long long* queue) {
     p.sol = sol;
+    p.solc = sol;                       // near-critical rays of the mixed paths
+    p.solc.rtol = sol.crit_rtol;
+    p.solc.atol = sol.crit_atol;
     p.n_desc = n;
     // defaults: the FP64 path steps every lane in FP64 anyway, so it refills and
     // refines in small batches; the mixed paths batch their FP64 work harder
@@ -1438,14 +1618,18 @@ void fill_params(LaunchParams<N>& p, const ImageDesc* descs, int n, long long to
     p.tune.fp64_batch = shape.fp64_batch > 0 ? shape.fp64_batch : (sol.precision == 3 ? 1 : 16);
     p.tune.monitor_period = shape.monitor_period > 0 ? shape.monitor_period : 32;
     p.tune.fp64_wait = shape.fp64_wait > 0 ? shape.fp64_wait : 64;
+    p.tune.crit_stride = shape.crit_stride > 0 ? shape.crit_stride : 1;
+    p.tune.crit_refill = shape.crit_refill > 0 ? shape.crit_refill : 32;
     p.total = total;
     p.queue = queue;
     for (int i = 0; i < n; ++i) p.desc[i] = descs[i];
 }
 
-// Mixed-precision launches (tt_kernel_mixed.cu) and double-float launches
-// (tt_kernel_df.cu).
+// Mixed-precision launches (tt_kernel_mixed.cu, the prescribed split in
+// tt_kernel_split.cu) and double-float launches (tt_kernel_df.cu).
 cudaError_t launch_mixed(const ImageDesc* descs, int n, long long total, const SolverDesc& sol,
+                         const LaunchShape& shape, unsigned long long* queue, cudaStream_t stream);
+cudaError_t launch_split(const ImageDesc* descs, int n, long long total, const SolverDesc& sol,
                          const LaunchShape& shape, unsigned long long* queue, cudaStream_t stream);
 cudaError_t launch_df(const ImageDesc* descs, int n, long long total, int metric_mode, const SolverDesc& sol,
                       const LaunchShape& shape, unsigned long long* queue, cudaStream_t stream);

@@ -26,7 +26,7 @@ from typing import List, Optional
 
 import numpy as np
 
-FP64, MIXED, MIXED_PAIR, DOUBLE_FLOAT = 0, 1, 2, 3
+FP64, MIXED, MIXED_PAIR, DOUBLE_FLOAT, MIXED_SPLIT = 0, 1, 2, 3, 4
 REFINE_HENON, REFINE_HERMITE, REFINE_HENON64 = 0, 1, 2
 DOPRI5, CASH_KARP, FEHLBERG, GBS, VERLET = 0, 1, 2, 3, 4
 METRIC_KERR, METRIC_TABLE = 0, 1
@@ -64,7 +64,11 @@ class Scene:
     method: int = DOPRI5              # integrator (Verlet: fixed step h0 > 0)
     fp64_radius_factor: float = 0.0   # mixed paths, double-float on a table: extended-precision steps below
                                       # factor * r_h (0: 2, < 0: none)
-    fp64_pole_sin: float = 0.0        # the same, where sin(theta) < this (0: 0.3 mixed, none on a table; < 0: none)
+    fp64_pole_sin: float = 0.0        # the same, where sin(theta) < this (0: 0.3 mixed, none on the prescribed
+                                      # split and on a table; < 0: none)
+    critical_band: float = 0.0        # mixed paths: rays this close to the critical curve (units of M) are traced
+                                      # in double-float (0: 0.1, none on the prescribed split; < 0: none)
+    critical_rtol: float = 0.0        # their rtol = atol (0: 1e-10)
     # disk
     disk_enabled: int = 0
     r_in: float = 0.0            # <= 0: ISCO

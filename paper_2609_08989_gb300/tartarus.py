@@ -44,7 +44,8 @@ class TTSolver(C.Structure):
     _fields_ = [("method", C.c_int), ("precision", C.c_int), ("rtol", C.c_double), ("atol", C.c_double),
                 ("h0", C.c_double), ("h_min", C.c_double), ("max_steps", C.c_longlong),
                 ("horizon_eps", C.c_double), ("escape_factor", C.c_double), ("refine", C.c_int),
-                ("fp64_radius_factor", C.c_double), ("fp64_pole_sin", C.c_double)]
+                ("fp64_radius_factor", C.c_double), ("fp64_pole_sin", C.c_double),
+                ("critical_band", C.c_double), ("critical_rtol", C.c_double)]
 
 
 class TTDisk(C.Structure):
@@ -61,7 +62,7 @@ class TTOutputs(C.Structure):
 class TTTune(C.Structure):
     _fields_ = [("block", C.c_int), ("reg_variant", C.c_int), ("refill", C.c_int), ("blocks_per_sm", C.c_int),
                 ("crossing_batch", C.c_int), ("fp64_batch", C.c_int), ("monitor_period", C.c_int),
-                ("fp64_wait", C.c_int)]
+                ("fp64_wait", C.c_int), ("crit_stride", C.c_int), ("crit_refill", C.c_int)]
 
 
 class TTImage(C.Structure):
@@ -211,7 +212,8 @@ def solver_struct(sc: Scene) -> TTSolver:
     return TTSolver(method=sc.method, precision=sc.precision, rtol=sc.rtol, atol=sc.atol, h0=sc.h0, h_min=sc.h_min,
                     max_steps=sc.max_steps, horizon_eps=sc.horizon_eps, escape_factor=sc.escape_factor,
                     refine=sc.refine, fp64_radius_factor=sc.fp64_radius_factor,
-                    fp64_pole_sin=sc.fp64_pole_sin)
+                    fp64_pole_sin=sc.fp64_pole_sin, critical_band=sc.critical_band,
+                    critical_rtol=sc.critical_rtol)
 
 
 def _disk(sc: Scene) -> TTDisk:

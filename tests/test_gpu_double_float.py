@@ -87,16 +87,16 @@ def test_same_steps_as_fp64_path(T):
     assert ((a["steps"] == b["steps"]) & (a["rejects"] == b["rejects"])).mean() > 0.995
 
 
-# The tabulated metric, at the FP64 table path's bars: at rtol 1e-12 the
-# interpolated flow (its slopes cancel ~10^3-fold) carries rounding of the order
-# of the tolerance, so step decisions flip between any two correct
-# implementations; identical step sequences agree to 1e-8, diverged ones to 1e-6,
-# well inside the interpolant's own ~1e-6 distance from the closed-form metric.
+# The tabulated metric, at the FP64 table path's bars: the interpolated flow
+# (its slopes cancel ~10^3-fold) carries rounding that moves the step sizes, so
+# two correct implementations take different valid step sequences, which differ
+# by the integration's own error; every crossing is held to max(1e-9, 10 x the
+# oracle's own change at 0.5 to 2 times the tolerance).
 # |H| maxima: at rtol 1e-12 a ray's drift off H = 0 is set by the rounding of
 # the interpolated flow, which carries the pair's 2^-48 instead of 2^-53, so the
 # maxima run up to ~2^5 above the oracle's (33x seen on captured rays, whatever
 # the radius of the FP64 zone); compared within 2^6, and bounded absolutely.
-TABLE_BARS = dict(rel=1e-8, min_same_steps=0.0, rel_diverged=1e-6, h_ratio_only=True, h_ratio=64.0)
+TABLE_BARS = dict(rel=1e-9, min_same_steps=0.0, h_ratio_only=True, h_ratio=64.0)
 
 
 def _table_scene(orc, n):
@@ -105,10 +105,16 @@ def _table_scene(orc, n):
     return scenes.table_kerr(n, table=orc.kerr_table(1.0, a, 512, 256, rh, 1000.0))
 
 
-def test_table_metric(T, orc):
-    sc = _table_scene(orc, 48).replace(precision=scenes.DOUBLE_FLOAT)
+@pytest.mark.parametrize("rtol", [1e-12, 1e-10])
+def test_table_metric(T, orc, rtol):
+    sc = _table_scene(orc, 48).replace(precision=scenes.DOUBLE_FLOAT, rtol=rtol, atol=rtol)
     got = run(T, sc)
-    rep = parity.compare(orc, sc, got, orc.trace(sc), np.arange(sc.npix), **TABLE_BARS)
+    ref = orc.trace(sc)
+    spread = parity.tolerance_spread(orc, sc, np.arange(sc.npix), ref)
+    rep = parity.compare(orc, sc, got, ref, np.arange(sc.npix), spread=spread, **TABLE_BARS)
+    if rtol == 1e-10:
+        print("double-float table 48^2 rtol 1e-10:", rep)
+        return
     print("double-float table 48^2:", rep)
     assert got["h_max"][got["code"] == 0].max() < 2e-8
     assert got["h_max"].max() < 1e-5
@@ -128,4 +134,6 @@ def test_table_ragged_range(T, orc):
     # there and ends some at max_steps or h_min): no two agree on those
     sc = _table_scene(orc, 60).replace(ny=37, precision=scenes.DOUBLE_FLOAT)
     got = run(T, sc, pix_begin=517, pix_count=1111)
-    parity.compare(orc, sc, got, orc.trace(sc, pix_begin=517, npix=1111), np.arange(517, 517 + 1111), **TABLE_BARS)
+    pix = np.arange(517, 517 + 1111)
+    ref = orc.trace(sc, pix_begin=517, npix=1111)
+    parity.compare(orc, sc, got, ref, pix, spread=parity.tolerance_spread(orc, sc, pix, ref), **TABLE_BARS)

@@ -1,15 +1,18 @@
 """The mixed-precision paths against the FP64 oracle (rtol 1e-10) on the Kerr
-thin-disk scene.
+thin-disk scene, at the mixed path's bars: termination codes equal outside the
++-1e-6 M band around the critical curve; crossing counts equal except there
+or at a disk edge; the radius and g factor of EVERY crossing of every other
+pixel within 1e-5 relative; |H| <= 1e-6 on every escaped ray (evaluated in
+FP64 by the kernel) with the default extended-precision zones (within 2 r_+ of
+the hole and asin(0.3) of the axis) -- on every pixel at 256^2, on the
+benchmark's 2048^2 image (a seeded sample plus its photon-ring pixels) and on
+images of the 64-image batch.
 
-Bars: termination codes equal outside the band around the critical curve
-(width 1e-5 here: the FP32 stages move trajectories by ~1e-7 relative);
-crossing radii and g factors within 1e-5 relative on the primary crossing of
-every pixel outside that band (higher-order crossings orbit the photon region
-and amplify any difference exponentially, so they are reported, not gated);
-|H| <= 1e-6 on every escaped ray (evaluated in FP64 by the kernel) with the
-default extended-precision zones (within 2 r_+ of the hole and asin(0.3) of
-the axis), on the benchmark's 2048^2 image and on the 64-image batch; with the
-horizon zone switched off, at the 99.9th percentile.
+Photon-ring crossings (rays that circle the unstable photon orbits) amplify any
+perturbation by ~e^pi per circuit, FP32 stage rounding included: rays within
+critical_band (0.1 M) of the critical curve, picked out a priori from their
+radial potential, are traced in double-float.  Without that escalation the
+primary crossings still meet 1e-5 but higher-order ones reach ~1e-4.
 """
 import numpy as np
 import pytest
@@ -42,83 +45,120 @@ def ref256(orc):
     return sc, orc.trace(sc)
 
 
+def mixed(base, precision, **kw):
+    return base.replace(precision=precision, rtol=scenes.MIXED_RTOL, atol=scenes.MIXED_RTOL, **kw)
+
+
 @pytest.mark.parametrize("precision,fp64_factor,refine", [
     (scenes.MIXED, 0.0, scenes.REFINE_HENON), (scenes.MIXED_PAIR, 0.0, scenes.REFINE_HENON),
     (scenes.MIXED, -1.0, scenes.REFINE_HENON), (scenes.MIXED_PAIR, -1.0, scenes.REFINE_HENON),
     (scenes.MIXED_PAIR, 0.0, scenes.REFINE_HENON64)])
 def test_mixed_against_oracle(T, orc, ref256, precision, fp64_factor, refine):
     base, ref = ref256
-    sc = base.replace(precision=precision, rtol=scenes.MIXED_RTOL, atol=scenes.MIXED_RTOL,
-                      fp64_radius_factor=fp64_factor, refine=refine)
+    sc = mixed(base, precision, fp64_radius_factor=fp64_factor, refine=refine)
     got = run(T, sc)
-    bad = np.nonzero(got["code"] != ref["code"])[0]
-    for q in bad:
-        assert parity.in_band(orc, base, int(q), width=1e-5), "code differs at pixel %d" % q
-    same = (got["code"] == ref["code"]) & (got["n_cross"] == ref["n_cross"])
-    assert same.mean() > 0.995
-    m = same & (ref["r_cross"][0] != 0)
-    rel_r = np.abs(got["r_cross"][0, m] - ref["r_cross"][0, m]) / ref["r_cross"][0, m]
-    rel_g = np.abs(got["g"][0, m] - ref["g"][0, m]) / np.abs(ref["g"][0, m])
-    out_of_bar = np.nonzero(m)[0][(rel_r > 1e-5) | (rel_g > 1e-5)]
-    for q in out_of_bar:
-        assert parity.in_band(orc, base, int(q), width=1e-4), \
-            "primary crossing off by %.2e at pixel %d" % (rel_r.max(), q)
+    rep = parity.compare_mixed(orc, base, got, ref, np.arange(base.npix))
     esc = got["code"] == 0
-    print("mixed prec %d fp64x %.1f: r_cross p50 %.1e p99 %.1e max %.1e | g max %.1e | |H| esc max %.2e, "
-          "capt max %.2e | steps %.1f" % (precision, fp64_factor, np.median(rel_r), np.percentile(rel_r, 99),
-                                          rel_r.max(), rel_g.max(), got["h_max"][esc].max(),
-                                          got["h_max"][~esc].max() if (~esc).any() else 0.0,
-                                          (got["steps"] + got["rejects"]).mean()))
-    assert np.percentile(rel_r, 99) < 1e-5
-    over = np.nonzero(esc & (got["h_max"] > 1e-6))[0]
-    if len(over):
-        print("escaped rays above 1e-6:", [(int(q), float(got["h_max"][q])) for q in over[:10]])
+    print("mixed prec %d fp64x %.1f refine %d: %s | |H| esc max %.2e, capt max %.2e | attempts %.1f"
+          % (precision, fp64_factor, refine, rep, got["h_max"][esc].max(), got["h_max"][~esc].max(),
+             (got["steps"] + got["rejects"]).mean()))
+    assert rep["n2"] > 20                          # photon-ring crossings are there to be checked
     if fp64_factor == 0.0:
         assert got["h_max"][esc].max() <= 1e-6
     else:
+        # without the horizon zone a few escaped rays that passed near r_+ drift further
         assert np.percentile(got["h_max"][esc], 99.9) <= 1e-6
         assert got["h_max"][esc].max() <= 5e-6
 
 
+def test_without_escalation_photon_rings_drift(T, orc, ref256):
+    """critical_band < 0: every ray in FP32 stages.  Primary crossings stay within
+    1e-5; the photon-ring crossings do not (the reason for the escalation)."""
+    base, ref = ref256
+    got = run(T, mixed(base, scenes.MIXED_PAIR, critical_band=-1.0))
+    ok = (got["code"] == ref["code"]) & (got["n_cross"] == ref["n_cross"])
+    m = ok[None, :] & (ref["r_cross"] != 0)
+    er = np.where(m, np.abs(got["r_cross"] - ref["r_cross"]) / np.where(m, ref["r_cross"], 1.0), 0.0)
+    print("no escalation: r max per order %s" % er.max(axis=1))
+    assert er[0].max() <= 1e-5
+    assert er[1:].max() > 1e-5
+
+
 def test_mixed_full_size_sampled(T, orc):
+    """The 2048^2 image with the benchmark's launch: 1500 seeded pixels, plus every
+    pixel with three or more crossings and 1500 with two (the photon-ring rays)."""
     sc = scenes.kerr_disk_mixed(2048)
     got = run(T, sc)
     assert set(np.unique(got["code"])) <= {0, 1}
-    pix = scenes.sample_pixels(sc.npix, 1500, 23)
+    rng = np.random.default_rng(23)
+    ring3 = np.nonzero(got["n_cross"] >= 3)[0]
+    ring2 = np.nonzero(got["n_cross"] == 2)[0]
+    pix = np.unique(np.concatenate([scenes.sample_pixels(sc.npix, 1500, 23), ring3,
+                                    rng.choice(ring2, min(1500, len(ring2)), replace=False)])).astype(np.int64)
     ref = orc.trace_list(sc.replace(precision=scenes.FP64, rtol=1e-10, atol=1e-10), pix)
     sub = {k: (v[:, pix] if v.ndim == 2 else v[pix]) for k, v in got.items()}
-    same = (sub["code"] == ref["code"]) & (sub["n_cross"] == ref["n_cross"])
-    assert same.mean() > 0.99
-    m = same & (ref["r_cross"][0] != 0)
-    rel = np.abs(sub["r_cross"][0, m] - ref["r_cross"][0, m]) / ref["r_cross"][0, m]
-    assert np.percentile(rel, 99) < 1e-5
-    esc = sub["code"] == 0
-    assert np.percentile(sub["h_max"][esc], 99.9) <= 1e-6
+    rep = parity.compare_mixed(orc, sc, sub, ref, pix)
+    print("mixed pair 2048^2 sampled (%d pixels): %s" % (len(pix), rep))
+    assert rep["n2"] > 1000
     # every escaped ray of the whole image
-    assert got["h_max"][got["code"] == 0].max() <= 1e-6
+    esc = got["code"] == 0
+    print("2048^2 |H| escaped max %.3e, captured max %.3e" % (got["h_max"][esc].max(), got["h_max"][~esc].max()))
+    assert got["h_max"][esc].max() <= 1e-6
 
 
-def test_mixed_batch_h_bound(T):
+def test_mixed_batch(T, orc):
     """The 64 uneven images (spins to 0.998, inclinations 5-85 deg, odd and even
     grids, so zero-angular-momentum rays through the axis too) in one launch:
-    |H| <= 1e-6 on every escaped ray."""
+    |H| <= 1e-6 on every escaped ray; crossings of eight images against the
+    oracle on a seeded sample plus their photon-ring pixels."""
     imgs = scenes.batch_uneven(64, seed=2609, precision=scenes.MIXED_PAIR)
     outs = T.trace_batch(imgs)
     torch.cuda.synchronize()
     worst = 0.0
-    for sc, o in zip(imgs, outs):
+    for k, (sc, o) in enumerate(zip(imgs, outs)):
         got = T.to_numpy(o)
         assert set(np.unique(got["code"])) <= {0, 1}
         esc = got["code"] == 0
         worst = max(worst, float(got["h_max"][esc].max()))
+        if k % 8 == 0:
+            ring = np.nonzero(got["n_cross"] >= 2)[0]
+            ring = np.random.default_rng(k).choice(ring, min(200, len(ring)), replace=False) if len(ring) else ring
+            pix = np.unique(np.concatenate([scenes.sample_pixels(sc.npix, 200, k), ring])).astype(np.int64)
+            ref = orc.trace_list(sc.replace(precision=scenes.FP64, rtol=1e-10, atol=1e-10), pix)
+            sub = {f: (v[:, pix] if v.ndim == 2 else v[pix]) for f, v in got.items()}
+            rep = parity.compare_mixed(orc, sc, sub, ref, pix)
+            print("batch image %d (a %.3f, %.1f deg, %d^2): %s" % (k, sc.a, np.degrees(sc.theta_obs), sc.nx, rep))
     print("batch escaped |H| max %.3e" % worst)
     assert worst <= 1e-6
+
+
+def test_prescribed_split(T, orc, ref256):
+    """TT_MIXED_SPLIT: FP32 stages with the FP64 state accumulation, error norm,
+    step control, steps below 1.5 r_+ and crossing refinement.  Codes and primary
+    crossings meet the bars; its photon-ring crossings need the escalation too,
+    and without a polar zone rays passing near the axis drift past |H| = 1e-6."""
+    base, ref = ref256
+    got = run(T, mixed(base, scenes.MIXED_SPLIT))
+    ok = (got["code"] == ref["code"]) & (got["n_cross"] == ref["n_cross"])
+    assert np.all(got["code"] == ref["code"])
+    m = ok[None, :] & (ref["r_cross"] != 0)
+    er = np.where(m, np.abs(got["r_cross"] - ref["r_cross"]) / np.where(m, ref["r_cross"], 1.0), 0.0)
+    esc = got["code"] == 0
+    print("prescribed split: r max per order %s, |H| esc max %.2e p99 %.2e" % (
+        er.max(axis=1), got["h_max"][esc].max(), np.percentile(got["h_max"][esc], 99)))
+    assert er[0].max() <= 1e-5
+    assert np.percentile(got["h_max"][esc], 99) <= 1e-6
+    # with the near-critical rays in double-float, every crossing meets the bar
+    esc_run = run(T, mixed(base, scenes.MIXED_SPLIT, critical_band=0.1))
+    rep = parity.compare_mixed(orc, base, esc_run, ref, np.arange(base.npix))
+    print("prescribed split with escalation:", rep)
 
 
 def test_mixed_table_is_unsupported(T, orc):
     import math
     a = 0.998
     nodes = orc.kerr_table(1.0, a, 16, 16, 1.0 + math.sqrt(1 - a * a), 1000.0)
-    sc = scenes.table_kerr(8, table=nodes).replace(precision=scenes.MIXED)
-    with pytest.raises(T.TartarusError):
-        run(T, sc)
+    for prec in (scenes.MIXED, scenes.MIXED_SPLIT):
+        sc = scenes.table_kerr(8, table=nodes).replace(precision=prec)
+        with pytest.raises(T.TartarusError):
+            run(T, sc)

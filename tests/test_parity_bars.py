@@ -1,0 +1,65 @@
+"""The parity bar for integrations whose step sequence is not fixed to rounding
+(tabulated metric, extrapolator): every crossing within max(1e-9, 10 x the
+oracle's own change at 0.5 to 2 times the tolerance).  Checked on the CPU with
+the oracle alone: a third valid integration (the same scene with its camera
+moved by 1e-15 relative) passes the bar, and an error planted in the crossing
+radii of the pixels that the bar holds to well below it fails it (1e-7 on the
+table at rtol 1e-12, 1e-6 at rtol 1e-10, where the interpolated integration
+itself is determined to only ~1e-8; 1e-8 for the extrapolator)."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2609_08989_gb300 import scenes
+import parity
+
+
+def table_scene(orc, n, rtol):
+    a = 0.998
+    rh = 1.0 + math.sqrt(1 - a * a)
+    return scenes.table_kerr(n, table=orc.kerr_table(1.0, a, 512, 256, rh, 1000.0)).replace(rtol=rtol, atol=rtol)
+
+
+def perturbed(sc, eps=1e-15):
+    return sc.replace(alpha_min=sc.alpha_min * (1 + eps), beta_max=sc.beta_max * (1 + eps))
+
+
+CASES = [("table", 1e-10), ("table", 1e-12), ("gbs", 1e-10)]
+PLANTED = {("table", 1e-10): 1e-6, ("table", 1e-12): 1e-7, ("gbs", 1e-10): 1e-8}
+
+
+def scene_for(orc, kind, rtol):
+    if kind == "table":
+        return table_scene(orc, 40, rtol)
+    return scenes.kerr_disk(64).replace(method=scenes.GBS, rtol=rtol, atol=rtol)
+
+
+@pytest.mark.parametrize("kind,rtol", CASES)
+def test_third_valid_integration_passes(orc, kind, rtol):
+    sc = scene_for(orc, kind, rtol)
+    pix = np.arange(sc.npix)
+    ref = orc.trace(sc)
+    spread = parity.tolerance_spread(orc, sc, pix, ref)
+    other = orc.trace(perturbed(sc))
+    rep = parity.compare(orc, sc, other, ref, pix, rel=1e-9, min_same_steps=0.0, spread=spread,
+                         h_ratio_only=True, h_ratio=10.0)
+    print(kind, rtol, rep)
+    assert rep["r_cross_over_tol"] <= 1.0
+
+
+@pytest.mark.parametrize("kind,rtol", CASES)
+def test_planted_error_fails(orc, kind, rtol):
+    sc = scene_for(orc, kind, rtol)
+    pix = np.arange(sc.npix)
+    ref = orc.trace(sc)
+    spread = parity.tolerance_spread(orc, sc, pix, ref)
+    bad = {k: v.copy() for k, v in ref.items()}
+    err = PLANTED[(kind, rtol)]
+    # pixels whose primary crossing the bar holds to half the planted error or better
+    well = (ref["r_cross"][0] != 0) & (np.maximum(1e-9, parity.SPREAD_FACTOR * spread[0][0]) < 0.5 * err)
+    assert well.sum() > 20
+    bad["r_cross"][0, well] *= 1.0 + err
+    with pytest.raises(AssertionError):
+        parity.compare(orc, sc, bad, ref, pix, rel=1e-9, min_same_steps=0.0, spread=spread,
+                       h_ratio_only=True, h_ratio=10.0)
