@@ -6,9 +6,20 @@ ISCO to 30 M with up to 3 crossings).
 One step = one full image traced by one persistent launch of the tracer
 (every pixel: initial data, integration, events, crossing refinement,
 emission, constraint monitor).  Rank r of N traces its own image (weak
-scaling, no collective on the data path).
+scaling, no collective on the data path); with --shard the N ranks split one
+image into pixel ranges of whole 4-row bands balanced by the step counts of a
+previous trace of it (strong scaling; each rank keeps its slice, which
+distributed.gather_image can assemble on the host).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl tartarus|reference]
+Besides the headline, the line carries the other paths on the same scene:
+double-float at the headline's tolerance, the mixed paths on the 2048^2 image
+(with their FP32-pipe fraction), the prescribed FP64 split, the 64-image
+batch, the FP64 and double-float paths at the loosest tolerance that also
+meets the mixed path's accuracy (the equal-accuracy comparison), and the
+paper's other four integrators.  The roofline denominators are the FP64 and
+FP32 FMA rates measured by an FMA-chain probe at the start of the run.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl tartarus|reference] [--shard]
 """
 from __future__ import annotations
 
@@ -29,8 +40,10 @@ METRIC = "geodesics/sec (Kerr a=0.9, 1024², rtol 1e-10) FP64 vs mixed at |H|≤
 UNIT = "geodesics/s"
 SM_COUNT = 152
 SM_MAX_MHZ = 2070.0
-# FP64 pipe: 2 DFMA per clock per SM (measured 1.185 TFLOP/s at 1995 MHz with an FMA-chain probe)
-FP64_PEAK_TFLOPS = SM_COUNT * SM_MAX_MHZ * 1e6 * 2 * 2 / 1e12
+# Unit-count peaks at the maximum SM clock, for reference beside the measured ones:
+# 2 DFMA and 128 FFMA per clock per SM.
+FP64_PEAK_DERIVED = SM_COUNT * SM_MAX_MHZ * 1e6 * 2 * 2 / 1e12
+FP32_PEAK_DERIVED = SM_COUNT * SM_MAX_MHZ * 1e6 * 128 * 2 / 1e12
 # Algorithmic FP64 flops of one Dormand-Prince step attempt on the Kerr FP64 path,
 # counted from the kernel source of this build (FMA = 2; add, mul, reciprocal and
 # sqrt 1 each, the reciprocal's Newton refinement not counted; sin and cos 1 each,
@@ -58,19 +71,23 @@ METHOD_NAMES = {v: k for k, v in METHODS.items()}
 # The same count for an FP32 step of the mixed paths (the rearranged FP32 flow is 72;
 # its stages, norm and control as in the FP64 step before the h-scaling above).
 FLOPS_PER_STEP_F32 = 6 * 72 + 232 + 20 + 5
-FP32_PEAK_TFLOPS = SM_COUNT * SM_MAX_MHZ * 1e6 * 128 * 2 / 1e12
-# FP64 thread instructions per Dormand-Prince step attempt of the FP64 kernel, measured by ncu on
-# the 512^2 image (profiles/trace_kernel64_kerr_disk_1024.md): DFMA, DMUL, DADD
+# FP64 thread instructions per Dormand-Prince step attempt of the FP64 kernel, from ncu's
+# instruction counts on the 512^2 image: DFMA, DMUL, DADD
 FP64_ISSUED_PER_STEP = (281.2, 208.6, 19.5)
-# FP32 thread instructions (FFMA + FMUL + FADD) per double-float step attempt, measured by ncu
-# on the 512^2 image (profiles/trace_kernel_df_kerr_disk_1024.md)
+# FP32 thread instructions (FFMA + FMUL + FADD) per double-float step attempt, from ncu's
+# instruction counts on the 512^2 image
 DF_FP32_INST_PER_STEP = 4693
 BYTES_OUT_PER_PIXEL = 3 * 3 * 8 + 8 + 8 + 4 + 4 + 1 + 1
-# DRAM traffic of the FP64 tracer per ray: ncu's dram__bytes_read.sum + dram__bytes_write.sum of
-# the 512^2 capture (profiles/trace_kernel64_kerr_disk_1024.md) divided by its 262,144 rays
-TRAFFIC_BYTES_PER_RAY = (440320.0 + 0.0) / 262144.0
+# DRAM traffic of the FP64 tracer per launch on the 1024^2 image: ncu's
+# dram__bytes_read.sum + dram__bytes_write.sum of one full-size launch (None: not
+# captured for this build of the kernel)
+TRAFFIC_BYTES_1024 = None
 # host-to-device input of one step: the image descriptor (sizeof(tt::ImageDesc)) and the queue reset
-DESC_BYTES = 384 + 8
+DESC_BYTES = 384 + 16
+# The loosest tolerance at which the FP64 and double-float paths also keep |H| <= 1e-6 on
+# every escaped ray of the disk image and its crossings within 1e-5 of the rtol-1e-10
+# oracle (sweep over 1e-8, 1.5e-8, 2e-8, 3e-8: 3e-8 gives 1.29e-6)
+EQUAL_ACCURACY_RTOL = 2e-8
 
 
 def parse():
@@ -82,13 +99,16 @@ def parse():
     p.add_argument("--n", type=int, default=1024, help="camera resolution (default: the 1024^2 workload)")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="oracle sample budget per measurement")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--precision", default="fp64", choices=["fp64", "mixed", "mixed_pair", "double_float"],
+    p.add_argument("--precision", default="fp64", choices=["fp64", "mixed", "mixed_pair", "double_float",
+                                                            "mixed_split"],
                    help="path of the main measurement (default: the FP64 headline)")
-    p.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision objects")
+    p.add_argument("--no-mixed", action="store_true", help="skip the objects of the other paths")
     p.add_argument("--method", default="dopri5", choices=list(METHODS),
                    help="integrator of the FP64 run (default: Dormand-Prince, the headline)")
     p.add_argument("--no-pairs", action="store_true",
                    help="skip the objects of the other four integrators in the default line")
+    p.add_argument("--shard", action="store_true",
+                   help="N ranks split one image by pixel ranges balanced by a previous trace's step counts")
     p.add_argument("--workload", default="kerr_disk", choices=["kerr_disk", "batch", "table", "e3", "e5", "osiris"],
                    help="kerr_disk: the 1024^2 headline image (default); batch: 64 uneven images in one "
                         "persistent launch, replayed from a CUDA graph; table: the 4096^2 tabulated-metric image")
@@ -102,7 +122,7 @@ def dist_env():
     return rank, world, local
 
 
-PRECISIONS = {"fp64": 0, "mixed": 1, "mixed_pair": 2, "double_float": 3}
+PRECISIONS = {"fp64": 0, "mixed": 1, "mixed_pair": 2, "double_float": 3, "mixed_split": 4}
 
 
 def workload(n, precision="fp64", method="dopri5"):
@@ -142,29 +162,62 @@ def time_variant(T, sc, steps, warmup, flush, tune=None):
     return sum(ms) / len(ms), out
 
 
-def config_dict(sc, world):
-    return {"workload": sc.name, "nx": sc.nx, "ny": sc.ny, "a": sc.a, "theta_obs_deg": 60.0,
+def config_dict(sc, world, shard=False):
+    return {"workload": sc.name, "nx": sc.nx, "ny": sc.ny, "a": sc.a,
+            "theta_obs_deg": round(math.degrees(sc.theta_obs), 6),
             "r_obs": sc.r_obs, "field": [sc.alpha_min, sc.alpha_max], "rtol": sc.rtol, "atol": sc.atol,
             "integrator": METHOD_NAMES[sc.method], "disk": ["isco", sc.r_out], "max_crossings": sc.max_crossings,
-            "global_batch": sc.npix * world, "per_gpu_rays": sc.npix, "parallelism": "dp%d" % world,
+            "global_batch": sc.npix * (1 if shard else world), "per_gpu_rays": (sc.npix // world if shard else sc.npix),
+            "parallelism": ("shard%d" % world) if shard else ("dp%d" % world),
             "l2": "flushed between timed steps (256 MiB write); working set is a few MB of state + outputs"}
+
+
+def h_stats(out):
+    """|H| maxima of escaped and captured rays of a device output dict."""
+    import numpy as np
+    h = out["h_max"].cpu().numpy()
+    esc = out["code"].cpu().numpy() == 0
+    r = {}
+    if esc.any():
+        r.update({"h_max_escaped": float(h[esc].max()), "h_max_escaped_p99": float(np.percentile(h[esc], 99)),
+                  "h_max_escaped_median": float(np.median(h[esc]))})
+    if (~esc).any():
+        r.update({"h_max_captured": float(h[~esc].max()), "h_max_captured_median": float(np.median(h[~esc]))})
+    return r
+
+
+def attempts_of(out):
+    return int(out["steps"].sum().item() + out["rejects"].sum().item())
+
+
+def fp32_roofline(attempts, ms, peaks):
+    """Algorithmic FP32 flops of the mixed step over the kernel time, against the
+    measured FP32 FMA rate."""
+    ach = FLOPS_PER_STEP_F32 * attempts / (ms / 1e3) / 1e12
+    return {"bound": "alu", "achieved": ach, "peak": peaks["fp32"], "unit": "TFLOP/s",
+            "frac": ach / peaks["fp32"], "peak_source": peaks["fp32_source"],
+            "peak_derived": FP32_PEAK_DERIVED, "frac_of_derived": ach / FP32_PEAK_DERIVED,
+            "flops_per_unit": FLOPS_PER_STEP_F32, "traffic": None,
+            "unit_of_work": "step attempt, each counted as one FP32 Dormand-Prince step (the double-float "
+                            "steps of the zones and of near-critical rays, ~7x the FP32 work, are not "
+                            "counted extra)"}
 
 
 # ---------------------------------------------------------------------------
 # CPU oracle timing (the reference arm and the cpu_baseline object)
 # ---------------------------------------------------------------------------
 
-def time_oracle(sc, seconds, seed=7):
-    """Trace seeded random pixels of the scene with the oracle on all host cores
-    until about ``seconds`` of wall time have passed; returns (rays/s, rays, cores)."""
-    import numpy as np
+def time_oracle(sc, seconds, seed=7, nthreads=None):
+    """Trace seeded random pixels of the scene with the oracle (all host cores, or
+    nthreads) until about ``seconds`` of wall time have passed; returns
+    (rays/s, rays, threads, seconds)."""
     import oracle
     from paper_2609_08989_gb300 import scenes
     oracle.build()
-    cores = os.cpu_count() or 1
+    cores = nthreads or os.cpu_count() or 1
     rng_seed = seed
     done, t_used = 0, 0.0
-    chunk = 4096
+    chunk = 4096 if cores > 1 else 256
     while t_used < seconds:
         pix = scenes.sample_pixels(sc.npix, chunk, rng_seed)
         t0 = time.perf_counter()
@@ -178,25 +231,37 @@ def time_oracle(sc, seconds, seed=7):
     return done / t_used, done, cores, t_used
 
 
+def cpu_baseline(sc, seconds):
+    v, rays, cores, tsec = time_oracle(sc, seconds)
+    v1, rays1, _, t1 = time_oracle(sc, max(2.0, seconds / 3), seed=1007, nthreads=1)
+    return {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%d seeded random pixels of the %dx%d image (%.1f s, all %d host cores)"
+                      % (rays, sc.nx, sc.ny, tsec, cores),
+            "single_thread": {"value": v1, "unit": UNIT, "cores": 1,
+                              "sample": "%d seeded random pixels (%.1f s, one thread)" % (rays1, t1)}}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
     sc = workload(args.n)
-    vals = []
     for _ in range(args.warmup):
         time_oracle(sc, min(2.0, args.cpu_seconds / 4))
     tot_rays, tot_t = 0, 0.0
-    for _ in range(args.steps):
-        v, rays, cores, t = time_oracle(sc, args.cpu_seconds / max(1, args.steps) * 2)
-        vals.append(v)
+    for k in range(args.steps):
+        v, rays, cores, t = time_oracle(sc, args.cpu_seconds / max(1, args.steps) * 2, seed=7 + 1000 * k)
         tot_rays += rays
         tot_t += t
     value = tot_rays / tot_t
+    cfg = config_dict(sc, 1)
+    cfg["step"] = "one seeded sample of the image's pixels per step (%d pixels in all)" % tot_rays
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sc.npix / value,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+            "ms_per_step_note": "wall time per step; each step traces a bounded seeded sample of the image's "
+                                "pixels, and value = sampled pixels / wall time",
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": config_dict(sc, 1),
+            "data": "synthetic", "config": cfg,
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                              "sample": "%d seeded random pixels of the %dx%d image, all host cores"
                                        % (tot_rays, sc.nx, sc.ny)},
@@ -252,15 +317,144 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def measure_peaks(local):
+    """FP64 and FP32 FMA rates from the FMA-chain probe, with the SM clock seen meanwhile."""
+    from paper_2609_08989_gb300 import peaks
+    clocks = ClockSampler(local)
+    clocks.start()
+    p64 = peaks.measure(True, seconds=0.5)
+    p32 = peaks.measure(False, seconds=0.5)
+    clk = clocks.stop()
+    src = "FMA-chain probe in this run (best of 3 launches of ~0.5 s; median SM clock %s MHz)" % (
+        clk["sm_mhz"] if clk else "not sampled")
+    return {"fp64": p64["tflops"], "fp32": p32["tflops"], "fp64_source": "FP64 " + src, "fp32_source": "FP32 " + src,
+            "clocks": clk}
+
+
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
+
+def other_paths(T, args, flush, peaks, main_sc):
+    """The double-float, mixed, prescribed-split, batch and equal-accuracy objects."""
+    import torch
+    from paper_2609_08989_gb300 import scenes
+    objs = {}
+    reps = max(2, args.steps // 2)
+    # the double-float path on the headline image itself (same tolerance, FP64-class results)
+    dsc = workload(args.n, "double_float")
+    ms, dout = time_variant(T, dsc, reps, 1, flush)
+    att = attempts_of(dout)
+    eq = FLOPS_PER_STEP * att / (ms / 1e3) / 1e12
+    inst = DF_FP32_INST_PER_STEP * att / (ms / 1e3)
+    objs["double_float"] = dict(
+        {"value": dsc.npix / (ms / 1e3), "unit": UNIT, "ms_per_image": ms, "workload": dsc.name,
+         "rtol": dsc.rtol, "arithmetic": "every stage in FP32-pair (double-float, ~48-bit) on the FP32 pipe",
+         "rk_step_attempts_per_image": att,
+         "fp64_equivalent_tflops": eq, "fp64_equivalent_vs_fp64_peak": eq / peaks["fp64"],
+         "fp32_pipe": {"instructions_per_step": DF_FP32_INST_PER_STEP, "achieved_ginst_per_s": inst / 1e9,
+                       "peak_ginst_per_s": peaks["fp32"] / 2 * 1e3, "frac": inst / (peaks["fp32"] / 2 * 1e12),
+                       "source": "FP32 thread instructions per step from ncu's instruction counts (512^2 image) "
+                                 "over the FMA rate measured in this run"}}, **h_stats(dout))
+    # the mixed paths on the same scene at 2048^2 (rtol 1e-8, |H| <= 1e-6 on escaped rays)
+    for name in ("mixed", "mixed_pair", "mixed_split"):
+        msc = workload(2 * args.n, name)
+        ms, mout = time_variant(T, msc, reps, 1, flush)
+        att = attempts_of(mout)
+        objs[name] = dict({"value": msc.npix / (ms / 1e3), "unit": UNIT, "ms_per_image": ms,
+                           "workload": msc.name, "rtol": msc.rtol, "rk_step_attempts_per_image": att,
+                           "roofline": fp32_roofline(att, ms, peaks)}, **h_stats(mout))
+    objs["mixed"]["arithmetic"] = ("FP32 stages, norm and control; FP64 state; double-float steps within 2 r_+ "
+                                   "and asin(0.3) of the axis; rays within 0.1 M of the critical curve traced "
+                                   "in double-float at rtol 1e-10")
+    objs["mixed_pair"]["arithmetic"] = objs["mixed"]["arithmetic"].replace("FP64 state", "compensated FP32-pair state")
+    objs["mixed_split"]["arithmetic"] = ("the prescribed split: FP32 stages; FP64 state, error norm and step "
+                                         "control; FP64 steps within 1.5 r_+; FP64 crossing refinement")
+    # mixed pair without the near-critical escalation (every ray in FP32 stages)
+    msc = workload(2 * args.n, "mixed_pair").replace(critical_band=-1.0)
+    ms, mout = time_variant(T, msc, reps, 1, flush)
+    objs["mixed_pair_no_escalation"] = {
+        "value": msc.npix / (ms / 1e3), "unit": UNIT, "ms_per_image": ms, "workload": msc.name,
+        "rk_step_attempts_per_image": attempts_of(mout), "roofline": fp32_roofline(attempts_of(mout), ms, peaks),
+        "note": "primary crossings within 1e-5 of the oracle; photon-ring crossings up to ~1e-4"}
+    # the 64-image batch (C4): one persistent launch, replayed from a CUDA graph
+    imgs = scenes.batch_uneven(64, seed=2609, precision=scenes.MIXED_PAIR)
+    rays = sum(s.npix for s in imgs)
+    graph = T.TraceGraph(imgs)
+    graph.replay()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    bms = []
+    for k in range(reps):
+        flush.fill_(k & 0xFF)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        graph.replay()
+        b.record(stream)
+        torch.cuda.synchronize()
+        bms.append(a.elapsed_time(b))
+    ms = sum(bms) / len(bms)
+    batt = sum(attempts_of(o) for o in graph.outs)
+    hesc = max(float(o["h_max"][o["code"] == 0].max().item()) for o in graph.outs)
+    objs["batch"] = {"value": rays / (ms / 1e3), "unit": UNIT, "ms_per_replay": ms, "rays": rays,
+                     "workload": "batch_uneven_64_images_seed2609_mixed_pair", "images": 64,
+                     "res": [min(s.nx for s in imgs), max(s.nx for s in imgs)], "rtol": imgs[0].rtol,
+                     "launch": "CUDA graph replay of one tartarus_trace_batch call (%d launch)"
+                               % graph.launches_per_replay,
+                     "rk_step_attempts": batt, "h_max_escaped": hesc,
+                     "roofline": fp32_roofline(batt, ms, peaks)}
+    # equal accuracy: the FP64 and double-float paths on the mixed paths' 2048^2 image at the
+    # loosest tolerance that also keeps |H| <= 1e-6 on escaped rays and crossings within 1e-5
+    eqa = {}
+    for name in ("fp64", "double_float"):
+        esc = workload(2 * args.n, name).replace(rtol=EQUAL_ACCURACY_RTOL, atol=EQUAL_ACCURACY_RTOL,
+                                                 name="kerr_a0.9_i60_disk_%d_rtol2e-8" % (2 * args.n))
+        ms, eout = time_variant(T, esc, 2, 1, flush)
+        eqa[name] = dict({"value": esc.npix / (ms / 1e3), "unit": UNIT, "ms_per_image": ms,
+                          "workload": esc.name, "rtol": esc.rtol, "rk_step_attempts_per_image": attempts_of(eout)},
+                         **h_stats(eout))
+    mp = objs["mixed_pair"]["value"]
+    eqa["mixed_pair_over_fp64"] = mp / eqa["fp64"]["value"]
+    eqa["mixed_pair_over_double_float"] = mp / eqa["double_float"]["value"]
+    eqa["note"] = ("rtol 2e-8 is the loosest of 1e-8, 1.5e-8, 2e-8, 3e-8 at which the FP64 path keeps |H| <= 1e-6 "
+                   "on every escaped ray (3e-8: 1.3e-6); its crossings are then within 1e-6 of the rtol-1e-10 "
+                   "oracle, the mixed pair's within 1e-5")
+    objs["equal_accuracy"] = eqa
+    return objs
+
+
+def integrator_objects(T, args, flush, peaks):
+    """The other four integrators of Sec. 3.2 on the same scene and tolerance
+    (Verlet: fixed step VERLET_H on a VERLET_N^2 camera, which it needs ~10^5 steps per ray for)."""
+    import numpy as np
+    pairs = {}
+    for name in ("cash_karp", "fehlberg", "gbs", "verlet"):
+        psc = workload(VERLET_N if name == "verlet" else args.n, "fp64", name)
+        ms, pout = time_variant(T, psc, 2, 1, flush)
+        h = pout["h_max"].cpu().numpy()
+        code = pout["code"].cpu().numpy()
+        esc = code == 0
+        att = attempts_of(pout)
+        pairs[name] = {"value": psc.npix / (ms / 1e3), "unit": UNIT, "ms_per_image": ms,
+                       "workload": psc.name, "step_attempts_per_image": att,
+                       "steps_per_ray": att / psc.npix,
+                       "h_max_escaped_median": float(np.median(h[esc])) if esc.any() else None,
+                       "h_max_escaped": float(h[esc].max()) if esc.any() else None,
+                       "captured": int((code == 1).sum()), "other_codes": int((code > 1).sum())}
+        if psc.method in FLOPS_PER_STEP_METHOD:
+            pach = FLOPS_PER_STEP_METHOD[psc.method] * att / (ms / 1e3) / 1e12
+            pairs[name].update({"fp64_tflops": pach, "frac": pach / peaks["fp64"]})
+        else:
+            pairs[name].update({"h0": psc.h0, "horizon_eps": psc.horizon_eps,
+                                "note": "flops per step vary with the fixed-point iterations: no roofline"})
+    return pairs
+
 
 def run_tartarus(args):
     import numpy as np
     import torch
     import torch.distributed as dist
-    from paper_2609_08989_gb300 import tartarus as T
+    from paper_2609_08989_gb300 import distributed as D, tartarus as T
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
@@ -268,13 +462,31 @@ def run_tartarus(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     sc = workload(args.n, args.precision, args.method)
     T.lib()
-    out = T.alloc_outputs(sc.npix)
+    peaks = measure_peaks(local)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
+    shard = args.shard and world > 1
+    if shard:
+        # one image split over the ranks by pixel ranges, balanced by the step counts
+        # of a previous trace of the same image (each rank traces it once, in full)
+        probe = T.trace(sc)
+        torch.cuda.synchronize()
+        weights = (probe["steps"] + probe["rejects"]).to(torch.float64)
+        if world > 1:
+            dist.all_reduce(weights)                   # identical on every rank; makes the split agree
+            weights /= world
+        begin, count = D.pixel_range(sc.npix, rank, world, weights=weights.cpu().numpy(), align=4 * sc.nx)
+        del probe
+    else:
+        begin, count = 0, sc.npix
+    out = T.alloc_outputs(max(count, 1))
+
+    def trace_step(s=stream):
+        T.trace(sc, out=out, stream=s, pix_begin=begin, pix_count=count)
 
     for k in range(max(args.warmup, 0)):
         flush.fill_(k & 0xFF)                     # first touch of the flush buffer stays out of the timing
-        T.trace(sc, out=out)
+        trace_step()
     torch.cuda.synchronize()
 
     def barrier():
@@ -285,7 +497,6 @@ def run_tartarus(args):
     clocks = ClockSampler(local)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     launches0 = T.launch_count()
-    step_attempts = 0
     barrier()
     clocks.start()
     t_begin = torch.cuda.Event(enable_timing=True)
@@ -294,143 +505,108 @@ def run_tartarus(args):
     for k in range(args.steps):
         flush.fill_(k & 0xFF)                     # L2 flush between timed steps
         ev[k][0].record(stream)
-        T.trace(sc, out=out, stream=stream)
+        trace_step()
         ev[k][1].record(stream)
     t_end.record(stream)
     barrier()
     clk = clocks.stop()
     launches = T.launch_count() - launches0
-    step_attempts = int(out["steps"].sum().item() + out["rejects"].sum().item())
+    step_attempts = attempts_of(out)
     total_ms = t_begin.elapsed_time(t_end)
     kern_ms = [a.elapsed_time(b) for a, b in ev]
     t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
     if world > 1:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     total_ms = float(t.item())
-    value = world * sc.npix * args.steps / (total_ms / 1e3)
+    rays_per_step = sc.npix if shard else world * sc.npix
+    value = rays_per_step * args.steps / (total_ms / 1e3)
     mean_kern = sum(kern_ms) / len(kern_ms)
+    att_all = torch.tensor([step_attempts], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(att_all)
+    attempts_total = float(att_all.item())
+    hst = h_stats(out)
+    spread = None
+    if shard:
+        # per-rank work spread of the balanced split: attempts and kernel time
+        w = torch.tensor([float(step_attempts), mean_kern], dtype=torch.float64, device="cuda")
+        allw = [torch.zeros_like(w) for _ in range(world)]
+        dist.all_gather(allw, w)
+        spread = {"attempts_per_rank": [float(x[0]) for x in allw], "kernel_ms_per_rank": [float(x[1]) for x in allw]}
 
     # end to end through the host-buffer entry point (outputs copied to pinned host memory)
-    host = T.alloc_host_outputs(sc.npix)
-    T.trace_host(sc, out=host)
+    host = T.alloc_host_outputs(max(count, 1))
+    T.trace_host(sc, out=host, pix_begin=begin, pix_count=count)
     barrier()
     e0 = time.perf_counter()
     for _ in range(args.steps):
-        T.trace_host(sc, out=host)
+        T.trace_host(sc, out=host, pix_begin=begin, pix_count=count)
         _ = float(host["intensity"][0])           # the host reads the result
     barrier()
     e2e_s = time.perf_counter() - e0
     tt = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
     if world > 1:
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-    e2e_value = world * sc.npix * args.steps / float(tt.item())
+    e2e_value = rays_per_step * args.steps / float(tt.item())
 
-    mixed = {}
-    if not args.no_mixed and args.precision == "fp64":
-        # the double-float path on the headline image itself (same tolerance, FP64-class results)
-        dsc = workload(args.n, "double_float")
-        ms, dout = time_variant(T, dsc, max(2, args.steps // 2), 1, flush)
-        h = dout["h_max"].cpu().numpy()
-        esc = dout["code"].cpu().numpy() == 0
-        att = int(dout["steps"].sum().item() + dout["rejects"].sum().item())
-        eq = FLOPS_PER_STEP * att / (ms / 1e3) / 1e12
-        mixed["double_float"] = {
-            "value": dsc.npix / (ms / 1e3), "unit": UNIT, "ms_per_image": ms, "workload": dsc.name,
-            "rtol": dsc.rtol, "arithmetic": "every stage in FP32-pair (double-float, ~48-bit) on the FP32 pipe",
-            "h_max_escaped": float(h[esc].max()) if esc.any() else None,
-            "h_max_escaped_p99": float(np.percentile(h[esc], 99)) if esc.any() else None,
-            "rk_step_attempts_per_image": att,
-            "fp64_equivalent_tflops": eq, "fp64_equivalent_vs_fp64_peak": eq / FP64_PEAK_TFLOPS,
-            "fp32_pipe": {"instructions_per_step": DF_FP32_INST_PER_STEP,
-                          "achieved_ginst_per_s": DF_FP32_INST_PER_STEP * att / (ms / 1e3) / 1e9,
-                          "peak_ginst_per_s": FP32_PEAK_TFLOPS / 2 * 1e3,
-                          "frac": DF_FP32_INST_PER_STEP * att / (ms / 1e3) / (FP32_PEAK_TFLOPS / 2 * 1e12),
-                          "source": "FP32 thread instructions per step from the 512^2 ncu capture "
-                                    "(profiles/trace_kernel_df_kerr_disk_1024.md)"}}
-        # the mixed-precision paths on the same Kerr disk scene at 2048^2, each at
-        # the tolerance that keeps |H| <= 1e-6 on escaped rays
-        for name in ("mixed", "mixed_pair"):
-            msc = workload(2 * args.n, name)
-            ms, mout = time_variant(T, msc, max(2, args.steps // 2), 1, flush)
-            h = mout["h_max"].cpu().numpy()
-            code = mout["code"].cpu().numpy()
-            esc = code == 0
-            mixed[name] = {"value": msc.npix / (ms / 1e3), "unit": UNIT, "ms_per_image": ms,
-                           "workload": msc.name, "rtol": msc.rtol,
-                           "accumulation": "fp64" if name == "mixed" else "compensated fp32 pair",
-                           "h_max_escaped": float(h[esc].max()) if esc.any() else None,
-                           "h_max_escaped_p99": float(np.percentile(h[esc], 99)) if esc.any() else None,
-                           "h_max_captured": float(h[~esc].max()) if (~esc).any() else None,
-                           "rk_step_attempts_per_image": int(mout["steps"].sum().item() + mout["rejects"].sum().item())}
+    objs = {}
+    if not args.no_mixed and args.precision == "fp64" and not shard:
+        objs = other_paths(T, args, flush, peaks, sc)
     pairs = {}
-    if not args.no_pairs and args.precision == "fp64" and args.method == "dopri5":
-        # the other four integrators of Sec. 3.2 on the same scene and tolerance
-        # (Verlet: fixed step VERLET_H on a VERLET_N^2 camera, which it needs ~10^5 steps per ray for)
-        for name in ("cash_karp", "fehlberg", "gbs", "verlet"):
-            psc = workload(VERLET_N if name == "verlet" else args.n, "fp64", name)
-            ms, pout = time_variant(T, psc, max(2, args.steps // 2), 1, flush)
-            h = pout["h_max"].cpu().numpy()
-            code = pout["code"].cpu().numpy()
-            esc = code == 0
-            att = int(pout["steps"].sum().item() + pout["rejects"].sum().item())
-            pairs[name] = {"value": psc.npix / (ms / 1e3), "unit": UNIT, "ms_per_image": ms,
-                           "workload": psc.name, "step_attempts_per_image": att,
-                           "steps_per_ray": att / psc.npix,
-                           "h_max_escaped_median": float(np.median(h[esc])) if esc.any() else None,
-                           "h_max_escaped": float(h[esc].max()) if esc.any() else None,
-                           "captured": int((code == 1).sum()), "other_codes": int((code > 1).sum())}
-            if psc.method in FLOPS_PER_STEP_METHOD:
-                pach = FLOPS_PER_STEP_METHOD[psc.method] * att / (ms / 1e3) / 1e12
-                pairs[name].update({"fp64_tflops": pach, "frac": pach / FP64_PEAK_TFLOPS})
-            else:
-                pairs[name].update({"h0": psc.h0, "horizon_eps": psc.horizon_eps,
-                                    "note": "flops per step vary with the fixed-point iterations: no roofline"})
+    if not args.no_pairs and args.precision == "fp64" and args.method == "dopri5" and not shard:
+        pairs = integrator_objects(T, args, flush, peaks)
     if rank == 0:
         fpu = FLOPS_PER_STEP_METHOD.get(sc.method, 0)
         achieved = fpu * step_attempts / (mean_kern / 1e3) / 1e12
+        issued = 2 * FP64_ISSUED_PER_STEP[0] + sum(FP64_ISSUED_PER_STEP[1:])
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": config_dict(sc, world),
-            "rk_steps_per_s": world * step_attempts * args.steps / (total_ms / 1e3),
-            "rk_step_attempts_per_image": step_attempts,
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": achieved / FP64_PEAK_TFLOPS,
-                         "traffic": (TRAFFIC_BYTES_PER_RAY * sc.npix
-                                     if args.precision == "fp64" and sc.method == 0 else None),
-                         "traffic_note": "bytes per launch, scaled from a 512^2 ncu capture by rays",
+            "scaling": "strong" if shard else "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_dict(sc, world, shard),
+            "rk_steps_per_s": attempts_total * args.steps / (total_ms / 1e3),
+            "rk_step_attempts_per_image": step_attempts if not shard else attempts_total,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peaks["fp64"], "unit": "TFLOP/s",
+                         "frac": achieved / peaks["fp64"], "peak_source": peaks["fp64_source"],
+                         "peak_derived": FP64_PEAK_DERIVED, "frac_of_derived": achieved / FP64_PEAK_DERIVED,
+                         "traffic": (TRAFFIC_BYTES_1024 * count / (1024 * 1024)
+                                     if TRAFFIC_BYTES_1024 and args.precision == "fp64" and sc.method == 0 else None),
+                         "traffic_note": "DRAM bytes of one full-size launch (ncu), scaled by the pixels traced",
                          "kernel": ("trace_kernel64_b256<0,1>" if sc.method == 0
                                     else "trace_kernel_rk<%d,0,1,256>" % sc.method), "kernel_ms": mean_kern,
-                         "peak_source": "FP64 pipe: 152 SMs x 2070 MHz x 2 DFMA/clk (derived)",
                          "flops_per_unit": fpu,
                          "unit_of_work": "%s step attempt" % METHOD_NAMES[sc.method],
-                         "issued": ({"fp64_flops_per_unit": 2 * FP64_ISSUED_PER_STEP[0] + sum(FP64_ISSUED_PER_STEP[1:]),
-                                     "tflops": (2 * FP64_ISSUED_PER_STEP[0] + sum(FP64_ISSUED_PER_STEP[1:]))
-                                               * step_attempts / (mean_kern / 1e3) / 1e12,
-                                     "frac": (2 * FP64_ISSUED_PER_STEP[0] + sum(FP64_ISSUED_PER_STEP[1:]))
-                                             * step_attempts / (mean_kern / 1e3) / 1e12 / FP64_PEAK_TFLOPS,
-                                     "source": "DFMA x 2 + DMUL + DADD per step from the 512^2 ncu capture"}
+                         "issued": ({"fp64_flops_per_unit": issued,
+                                     "tflops": issued * step_attempts / (mean_kern / 1e3) / 1e12,
+                                     "frac": issued * step_attempts / (mean_kern / 1e3) / 1e12 / peaks["fp64"],
+                                     "source": "DFMA x 2 + DMUL + DADD per step from ncu's instruction counts "
+                                               "(512^2 image)"}
                                     if sc.method == 0 else None)},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": DESC_BYTES,
-                    "d2h_bytes_per_step": BYTES_OUT_PER_PIXEL * sc.npix},
+                    "d2h_bytes_per_step": BYTES_OUT_PER_PIXEL * count},
             "gpu_launches": launches,
             "clocks": clk,
+            "peaks": {"fp64_tflops": peaks["fp64"], "fp32_tflops": peaks["fp32"], "clocks": peaks["clocks"],
+                      "fp64_derived": FP64_PEAK_DERIVED, "fp32_derived": FP32_PEAK_DERIVED},
         }
+        line.update(hst)
+        if spread:
+            line["shard"] = spread
         if args.precision != "fp64":
             line["dtype"] = {"mixed": "f32 stages / f64 state", "mixed_pair": "f32 stages / f32-pair state",
-                             "double_float": "f32 pair (double-float)"}[args.precision]
-            line["roofline"] = None          # the FP64 flop count does not describe the mixed step
+                             "double_float": "f32 pair (double-float)",
+                             "mixed_split": "f32 stages / f64 state, norm, zones"}[args.precision]
+            if args.precision == "double_float":
+                line["roofline"] = None
+            else:
+                line["roofline"] = fp32_roofline(step_attempts, mean_kern, peaks)
         if sc.method not in FLOPS_PER_STEP_METHOD:
             line["roofline"] = None          # Verlet: flops per step vary with its fixed-point iterations
-        line.update(mixed)
+        line.update(objs)
         if pairs:
             line["integrators"] = pairs
         if not args.no_cpu_baseline:
-            v, rays, cores, tsec = time_oracle(sc, args.cpu_seconds)
-            line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-                                    "sample": "%d seeded random pixels of the %dx%d image (%.1f s)"
-                                              % (rays, sc.nx, sc.ny, tsec)}
+            line["cpu_baseline"] = cpu_baseline(sc, args.cpu_seconds)
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -448,6 +624,7 @@ def run_workload(args):
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     T.lib()
+    peaks = measure_peaks(local)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
     table = None
@@ -524,32 +701,23 @@ def run_workload(args):
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
     total_ms = float(tt.item())
     kern_ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
-    attempts = int(sum(o["steps"].sum().item() + o["rejects"].sum().item() for o in outs))
+    attempts = int(sum(attempts_of(o) for o in outs))
     if rank == 0:
-        fpu = None
+        roof = None
         if args.workload == "batch":
-            fpu, flops = FLOPS_PER_STEP_F32, FLOPS_PER_STEP_F32 * attempts
-            peak, unit = FP32_PEAK_TFLOPS, "TFLOP/s"
-            work = "FP32 Dormand-Prince step attempt (FP64 side work not counted)"
-            src = "FP32 pipe: 152 SMs x 2070 MHz x 128 FFMA/clk (derived)"
+            roof = fp32_roofline(attempts, kern_ms, peaks)
         elif args.workload in ("e3", "e5", "osiris") and sc.method in FLOPS_PER_STEP_METHOD:
             fpu = FLOPS_PER_STEP_METHOD[sc.method]
-            flops, peak, unit = fpu * attempts, FP64_PEAK_TFLOPS, "TFLOP/s"
-            work = "%s step attempt" % args.method
-            src = "FP64 pipe: 152 SMs x 2070 MHz x 2 DFMA/clk (derived)"
-        else:
-            flops, peak, unit = None, FP64_PEAK_TFLOPS, "TFLOP/s"
+            ach = fpu * attempts / (kern_ms / 1e3) / 1e12
+            roof = {"bound": "alu", "achieved": ach, "peak": peaks["fp64"], "unit": "TFLOP/s",
+                    "frac": ach / peaks["fp64"], "traffic": None, "flops_per_unit": fpu,
+                    "unit_of_work": "%s step attempt" % args.method, "peak_source": peaks["fp64_source"]}
         line = {"metric": METRIC, "value": world * rays * args.steps / (total_ms / 1e3), "unit": UNIT,
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype,
                 "data": "synthetic", "config": cfg, "rk_step_attempts_per_step": attempts,
                 "gpu_launches": launches_per_step * args.steps, "clocks": clk,
-                "e2e": None}
-        if flops is not None:
-            ach = flops / (kern_ms / 1e3) / 1e12
-            line["roofline"] = {"bound": "alu", "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak,
-                                "traffic": None, "flops_per_unit": fpu, "unit_of_work": work,
-                                "peak_source": src}
+                "e2e": None, "roofline": roof}
         if args.workload in ("e3", "e5", "osiris"):
             # the paper's hardware-independent figure: wall time per photon per integration step
             line["ns_per_photon_step"] = total_ms / args.steps * 1e6 / max(attempts, 1)

@@ -564,13 +564,15 @@ static __device__ float initial_step32(const Lane& L, const StateF& y0, float dr
     return fminf(100.0f * h0, h1);
 }
 
-// A whole image whose sides are multiples of 8 and 4 is handed out in 8 x 4
-// pixel tiles (32 consecutive queue entries per tile), so that the rays a warp
-// takes together start close on the sky and stay in step: the queue entry q of
-// such an image traces the tile's pixel returned here.  Outputs are per pixel
-// either way.
+// An image (or a pixel range of whole rows) whose width is a multiple of 8 and
+// whose row count is a multiple of 4 is handed out in 8 x 4 pixel tiles (32
+// consecutive queue entries per tile), so that the rays a warp takes together
+// start close on the sky and stay in step: the queue entry q of such a range
+// traces the tile's pixel returned here (relative to the range's first pixel).
+// Outputs are per pixel either way.
 __device__ __forceinline__ long long tile_pixel(const ImageDesc& d, long long q) {
-    if (d.pix_begin == 0 && d.pix_count == (long long)d.nx * d.ny && (d.nx & 7) == 0 && (d.ny & 3) == 0) {
+    const long long band = 4LL * d.nx;
+    if ((d.nx & 7) == 0 && d.pix_begin % band == 0 && d.pix_count % band == 0) {
         const long long tile = q >> 5, tiles_x = d.nx >> 3;
         const long long ty = tile / tiles_x, tx = tile - ty * tiles_x;
         const int lane = (int)(q & 31);

@@ -17,20 +17,29 @@ FIELDS_1D = ("code", "n_cross", "intensity", "h_max", "steps", "rejects")
 FIELDS_2D = ("r_cross", "g", "I_cross")
 
 
-def pixel_range(npix: int, rank: int, world: int, weights: Optional[np.ndarray] = None) -> Tuple[int, int]:
-    """[begin, begin + count) of the rank's share of npix pixels."""
+def pixel_range(npix: int, rank: int, world: int, weights: Optional[np.ndarray] = None,
+                align: int = 1) -> Tuple[int, int]:
+    """[begin, begin + count) of the rank's share of npix pixels.  align: the
+    interior cuts fall on multiples of it (e.g. 4 camera rows, so that every
+    range is traced in the tracer's 8 x 4 pixel tiles)."""
     if not 0 <= rank < world:
         raise ValueError("rank out of range")
+    if align < 1:
+        raise ValueError("align must be >= 1")
     if weights is None:
-        base, extra = divmod(npix, world)
-        begin = rank * base + min(rank, extra)
-        return begin, base + (1 if rank < extra else 0)
-    w = np.asarray(weights, dtype=np.float64)
+        if align == 1:
+            base, extra = divmod(npix, world)
+            begin = rank * base + min(rank, extra)
+            return begin, base + (1 if rank < extra else 0)
+        w = np.ones(npix)
+    else:
+        w = np.asarray(weights, dtype=np.float64)
     if w.shape != (npix,) or np.any(w < 0):
         raise ValueError("weights must be npix non-negative numbers")
     cum = np.concatenate([[0.0], np.cumsum(w)])
     total = cum[-1]
     cuts = [int(np.searchsorted(cum, total * k / world, side="left")) for k in range(world + 1)]
+    cuts = [min(npix, align * int(round(c / align))) for c in cuts]
     cuts[0], cuts[-1] = 0, npix
     for k in range(1, world + 1):
         cuts[k] = max(cuts[k], cuts[k - 1])
@@ -38,9 +47,9 @@ def pixel_range(npix: int, rank: int, world: int, weights: Optional[np.ndarray] 
 
 
 def trace_shard(trace: Callable[..., Dict[str, np.ndarray]], scene, rank: int, world: int,
-                weights: Optional[np.ndarray] = None) -> Tuple[int, Dict[str, np.ndarray]]:
+                weights: Optional[np.ndarray] = None, align: int = 1) -> Tuple[int, Dict[str, np.ndarray]]:
     """Trace this rank's pixel range with ``trace(scene, pix_begin, pix_count)``."""
-    begin, count = pixel_range(scene.nx * scene.ny, rank, world, weights)
+    begin, count = pixel_range(scene.nx * scene.ny, rank, world, weights, align)
     return begin, trace(scene, begin, count)
 
 
