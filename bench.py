@@ -84,10 +84,11 @@ BYTES_OUT_PER_PIXEL = 3 * 3 * 8 + 8 + 8 + 4 + 4 + 1 + 1
 TRAFFIC_BYTES_1024 = None
 # host-to-device input of one step: the image descriptor (sizeof(tt::ImageDesc)) and the queue reset
 DESC_BYTES = 384 + 16
-# The loosest tolerance at which the FP64 and double-float paths also keep |H| <= 1e-6 on
-# every escaped ray of the disk image and its crossings within 1e-5 of the rtol-1e-10
-# oracle (sweep over 1e-8, 1.5e-8, 2e-8, 3e-8: 3e-8 gives 1.29e-6)
-EQUAL_ACCURACY_RTOL = 2e-8
+# The tolerance of the equal-accuracy comparison: the mixed paths' own, at which the FP64
+# and double-float paths also keep |H| <= 1e-6 on every escaped ray of the 2048^2 disk
+# image (the next looser ones measured there, 2e-8 and 3e-8, give 1.1e-6 and more) and
+# their crossings within 1e-6 of the rtol-1e-10 oracle
+EQUAL_ACCURACY_RTOL = 1e-8
 
 
 def parse():
@@ -408,7 +409,8 @@ def other_paths(T, args, flush, peaks, main_sc):
     eqa = {}
     for name in ("fp64", "double_float"):
         esc = workload(2 * args.n, name).replace(rtol=EQUAL_ACCURACY_RTOL, atol=EQUAL_ACCURACY_RTOL,
-                                                 name="kerr_a0.9_i60_disk_%d_rtol2e-8" % (2 * args.n))
+                                                 name="kerr_a0.9_i60_disk_%d_rtol%g" % (2 * args.n,
+                                                                                          EQUAL_ACCURACY_RTOL))
         ms, eout = time_variant(T, esc, 2, 1, flush)
         eqa[name] = dict({"value": esc.npix / (ms / 1e3), "unit": UNIT, "ms_per_image": ms,
                           "workload": esc.name, "rtol": esc.rtol, "rk_step_attempts_per_image": attempts_of(eout)},
@@ -416,9 +418,9 @@ def other_paths(T, args, flush, peaks, main_sc):
     mp = objs["mixed_pair"]["value"]
     eqa["mixed_pair_over_fp64"] = mp / eqa["fp64"]["value"]
     eqa["mixed_pair_over_double_float"] = mp / eqa["double_float"]["value"]
-    eqa["note"] = ("rtol 2e-8 is the loosest of 1e-8, 1.5e-8, 2e-8, 3e-8 at which the FP64 path keeps |H| <= 1e-6 "
-                   "on every escaped ray (3e-8: 1.3e-6); its crossings are then within 1e-6 of the rtol-1e-10 "
-                   "oracle, the mixed pair's within 1e-5")
+    eqa["note"] = ("the FP64 and double-float paths at the mixed paths' rtol 1e-8, where they also keep |H| <= 1e-6 "
+                   "on every escaped ray (2e-8 gives 1.1e-6 on this image) and their crossings within 1e-6 of the "
+                   "rtol-1e-10 oracle; the mixed pair's crossings are within 1e-5")
     objs["equal_accuracy"] = eqa
     return objs
 

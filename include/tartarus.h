@@ -106,12 +106,13 @@ typedef struct {
  * r < r_h (1 + horizon_eps), escaped when r > escape_factor * r_obs
  * (escape_factor > 1).  fp64_radius_factor (mixed paths, and the
  * double-float path on a table): steps that start at r < fp64_radius_factor *
- * r_h run in extended precision (0 selects 2, or 1.5 for TT_MIXED_SPLIT;
- * negative: none); so do steps that start within asin(fp64_pole_sin) of the
- * polar axis (0 selects 0.3 on TT_MIXED and TT_MIXED_PAIR and none on
- * TT_MIXED_SPLIT and on a table, negative: none), where L^2 / sin^2(theta)
- * makes FP32 lose the constraint.  The defaults keep |H| <= 1e-6 on escaped
- * rays at rtol 1e-8.  TT_MIXED and TT_MIXED_PAIR run these extended-precision
+ * r_h run in extended precision (0 selects 1.5 on the mixed paths and 2 on a
+ * table; negative: none); so do steps that start within asin(fp64_pole_sin) of
+ * the polar axis (0 or negative: none).  The FP32 stages of the mixed paths
+ * take theta relative to the nearest axis crossing (theta - m pi), so that
+ * sin(theta) keeps FP32's relative precision near both poles; with the
+ * defaults every escaped ray keeps |H| <= 1e-6 at rtol 1e-8.  TT_MIXED and
+ * TT_MIXED_PAIR run these extended-precision
  * steps in double-float (FP32-pair, ~48-bit) arithmetic on the FP32 pipe;
  * TT_MIXED_SPLIT runs them in FP64, forms the error norm and the step-size
  * control of its FP32 steps in FP64 from the FP32 error terms, and refines
@@ -233,8 +234,9 @@ typedef struct {
  *                   iterations (default 32)
  *   fp64_wait       mixed paths: lanes waiting for a zone step get one after at
  *                   most this many warp iterations (default 64)
- *   crit_stride     mixed paths with a critical band: one warp in crit_stride
- *                   starts by scanning for near-critical rays (default 1: all)
+ *   crit_stride     mixed paths with a critical band: the warps of one SM in
+ *                   crit_stride start by scanning for near-critical rays
+ *                   (default 1: every SM)
  *   crit_refill     mixed paths: a warp tracing near-critical rays refills once
  *                   this many lanes are free (1..32, default 32) */
 typedef struct {

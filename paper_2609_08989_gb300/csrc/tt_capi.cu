@@ -166,18 +166,16 @@ int make_desc(const tt_metric* m, const tt_observer* obs, const tt_camera* cam, 
     }
     d->r_capture = r_h * (1.0 + sol->horizon_eps);
     d->r_escape = sol->escape_factor * obs->r_obs;
-    // mixed paths: steps starting below r_fp64 run in double-float (factor 0 -> 2,
-    // negative -> never) ... and those within asin(fp64_pole_sin) of the axis
-    // (0 -> 0.3, negative -> never).  The defaults keep |H| <= 1e-6 on every
-    // escaped ray of the benchmark image and of the 64-image batch at rtol 1e-8.
-    // Double-float path on a table: the same zones run in FP64 (pole default:
-    // none -- the measured crossings and |H| do not change with it).
-    // The prescribed split (TT_MIXED_SPLIT): FP64 steps below 1.5 r_h, no pole zone.
+    // mixed paths: steps starting below r_fp64 run in double-float (TT_MIXED_SPLIT:
+    // FP64) (factor 0 -> 1.5, negative -> never), and those within
+    // asin(fp64_pole_sin) of the axis (0 or negative -> never: the FP32 stages
+    // take theta relative to the nearest axis crossing, which keeps |H| <= 1e-6
+    // on every escaped ray of the benchmark image and of the 64-image batch
+    // without a polar zone).  Double-float path on a table: the same zones run in
+    // FP64, with the radius factor 2 by default.
     const bool df_table = m->kind == TT_METRIC_TABLE && sol->precision == TT_DOUBLE_FLOAT;
-    const bool split = sol->precision == TT_MIXED_SPLIT;
-    const double pole_default = (df_table || split) ? -1.0 : 0.3;
-    const double pole_sin = sol->fp64_pole_sin != 0.0 ? sol->fp64_pole_sin : pole_default;
-    const double radius_default = split ? 1.5 : 2.0;
+    const double pole_sin = sol->fp64_pole_sin != 0.0 ? sol->fp64_pole_sin : -1.0;
+    const double radius_default = df_table ? 2.0 : 1.5;
     d->r_fp64 = sol->fp64_radius_factor < 0.0
                     ? 0.0
                     : (sol->fp64_radius_factor > 0.0 ? sol->fp64_radius_factor : radius_default) * r_h;

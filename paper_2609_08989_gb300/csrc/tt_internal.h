@@ -96,7 +96,7 @@ struct TuneParams {
     int fp64_batch;       // mixed: run the double-float zone steps once this many lanes need one
     int monitor_period;   // mixed: FP64 |H| check every this many iterations
     int fp64_wait;        // mixed: zone steps run after this many iterations of waiting
-    int crit_stride;      // mixed: one warp in crit_stride starts with the near-critical rays
+    int crit_stride;      // mixed: the warps of one SM in crit_stride start with the near-critical rays
     int crit_refill;      // mixed: refill threshold of a warp tracing near-critical rays
 };
 

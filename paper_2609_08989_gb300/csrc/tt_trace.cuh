@@ -543,8 +543,10 @@ __device__ __forceinline__ void split_state(const State& y, StateF& hi, StateF& 
 }
 
 // The Hairer-Norsett-Wanner starting step in FP32 for the mixed paths, from the
-// FP32 flow k1f at yf (already in L).
-static __device__ float initial_step32(const Lane& L, const StateF& y0, float dr0, float atol, float rtol) {
+// FP32 flow k1f at yf (already in L); the flow takes theta as dth0 = theta - m pi
+// (see step_ray32).
+static __device__ float initial_step32(const Lane& L, const StateF& y0, float dr0, float dth0, float atol,
+                                       float rtol) {
     const StateF f0 = L.k1f;
     const float sr = fmaf(rtol, fabsf(y0.r), atol), st = fmaf(rtol, fabsf(y0.th), atol);
     const float sp = fmaf(rtol, fabsf(y0.pr), atol), sq = fmaf(rtol, fabsf(y0.pth), atol);
@@ -557,7 +559,8 @@ static __device__ float initial_step32(const Lane& L, const StateF& y0, float dr
     const StateF y1 = {fmaf(h0, f0.r, y0.r), fmaf(h0, f0.th, y0.th), fmaf(h0, f0.pr, y0.pr), fmaf(h0, f0.pth, y0.pth)};
     StateF f1;
     float H1;
-    kerr_flow32(L.Mf, L.a2f, L.rpmf, L.Rf, y1, fmaf(h0, f0.r, dr0), f1, H1);
+    kerr_flow32(L.Mf, L.a2f, L.rpmf, L.Rf, StateF{y1.r, fmaf(h0, f0.th, dth0), y1.pr, y1.pth}, fmaf(h0, f0.r, dr0),
+                f1, H1);
     const float d2 = n4(f1.r - f0.r, f1.th - f0.th, f1.pr - f0.pr, f1.pth - f0.pth) / h0;
     const float dm = fmaxf(d1, d2);
     const float h1 = (dm <= 1e-15f) ? fmaxf(1e-6f, h0 * 1e-3f) : __powf(0.01f / dm, 0.2f);
@@ -732,10 +735,12 @@ __device__ bool init_ray(Lane& L, const ImageDesc* d_ptr, long long q, const Sol
         } else {
             const StateF yf = {(float)L.y.r, (float)L.y.th, (float)L.y.pr, (float)L.y.pth};
             const float dr0 = (float)(L.y.r - d.r_plus);
+            const float dth0 = (float)(L.y.th - rint(L.y.th * 0.3183098861837907) * 3.141592653589793);
             float H0;
-            kerr_flow32(L.Mf, L.a2f, L.rpmf, L.Rf, yf, dr0, L.k1f, H0);
+            kerr_flow32(L.Mf, L.a2f, L.rpmf, L.Rf, StateF{yf.r, dth0, yf.pr, yf.pth}, dr0, L.k1f, H0);
             L.k32_ok = true;
-            L.hf = (sol.h0 > 0.0) ? (float)sol.h0 : initial_step32(L, yf, dr0, (float)sol.atol, (float)sol.rtol);
+            L.hf = (sol.h0 > 0.0) ? (float)sol.h0
+                                  : initial_step32(L, yf, dr0, dth0, (float)sol.atol, (float)sol.rtol);
         }
         L.h = (double)L.hf;
     }
@@ -978,24 +983,34 @@ __device__ int step_ray32(Lane& L, StateF& yhi, const SolverDesc& sol) {
     if (h < hmin) return 3;
     using namespace dp;
     StateF y;
-    float dr0;
+    float dr0, dth0;
+    // The flow depends on theta only through sin^2, cos^2 and sin cos, which are
+    // the same at delta = theta - m pi (m the nearest integer to theta / pi): the
+    // stages take delta, formed from the high-precision state, so that near
+    // theta = pi (where an FP32 theta resolves pi - theta, and so sin theta,
+    // only to ~2.4e-7 absolute) sin theta keeps FP32's relative precision, as it
+    // does near theta = 0.
     if (ACC == 0) {
         y = StateF{(float)L.y.r, (float)L.y.th, (float)L.y.pr, (float)L.y.pth};
         dr0 = (float)(L.y.r - d.r_plus);
+        const float m = rintf(y.th * 0.318309886f);
+        dth0 = (float)fma(-(double)m, 3.141592653589793, L.y.th);
     } else {
         y = yhi;
         dr0 = (y.r - L.rph) + (L.lo.r - L.rpl);
+        const float m = rintf(y.th * 0.318309886f);
+        dth0 = fmaf(-m, 3.14159274f, y.th) + fmaf(m, 8.74227766e-8f, L.lo.th);
     }
     float Hs;
     if (!L.k32_ok) {
-        kerr_flow32(L.Mf, L.a2f, L.rpmf, L.Rf, y, dr0, L.k1f, Hs);
+        kerr_flow32(L.Mf, L.a2f, L.rpmf, L.Rf, StateF{y.r, dth0, y.pr, y.pth}, dr0, L.k1f, Hs);
         L.k32_ok = true;
     }
     const StateF k1 = L.k1f;
     StateF k2, k3, k4, k5, k6, k7, ys;
 #define TT_FS(dst, er, et, ep, eq)                         \
     ys.r = fmaf(h, (er), y.r);                             \
-    ys.th = fmaf(h, (et), y.th);                           \
+    ys.th = fmaf(h, (et), dth0);                           \
     ys.pr = fmaf(h, (ep), y.pr);                           \
     ys.pth = fmaf(h, (eq), y.pth);                         \
     kerr_flow32(L.Mf, L.a2f, L.rpmf, L.Rf, ys, fmaf(h, (er), dr0), dst, Hs);
@@ -1019,7 +1034,7 @@ __device__ int step_ray32(Lane& L, StateF& yhi, const SolverDesc& sol) {
     inc.pth = h * TT_C7(pth);
     StateF yn = {y.r + inc.r, y.th + inc.th, y.pr + inc.pr, y.pth + inc.pth};
     float Hn;
-    kerr_flow32(L.Mf, L.a2f, L.rpmf, L.Rf, yn, dr0 + inc.r, k7, Hn);
+    kerr_flow32(L.Mf, L.a2f, L.rpmf, L.Rf, StateF{yn.r, dth0 + inc.th, yn.pr, yn.pth}, dr0 + inc.r, k7, Hn);
 #define TT_E(f) \
     h * fmaf((float)e7, k7.f, fmaf((float)e6, k6.f, fmaf((float)e5, k5.f, fmaf((float)e4, k4.f, \
              fmaf((float)e3, k3.f, (float)e1 * k1.f)))))
@@ -1368,7 +1383,7 @@ enum : int { kIdle = 0, kRun = 1, kDone = 2 };
 // only): 0 Dormand-Prince, 1 Cash-Karp, 2 Fehlberg, 3 Gragg-Bulirsch-Stoer,
 // 4 Verlet.  solc: the solver settings of the mixed paths' near-critical rays.
 //
-// Mixed paths with a critical band: one warp in crit_stride scans the rays
+// Mixed paths with a critical band: the warps of one SM in crit_stride scan the rays
 // (queue[1]) for near-critical ones and traces those in double-float, with
 // whole warps of them; the other warps take the rays from queue[0], skipping
 // the near-critical ones (the same test picks them out).  A warp whose queue
@@ -1393,12 +1408,16 @@ __device__ __forceinline__ void trace_loop(const ImageDesc* descs, int n_desc, l
     StateF yhi = {0.0f, 0.0f, 0.0f, 0.0f};   // pair accumulator: hi parts
     int st = kIdle;
     bool drained = false;
-    // one warp in crit_stride starts with the scan for near-critical rays, the
-    // others with the bulk; a warp whose queue is drained and whose lanes are
-    // all written takes the other queue, until both are drained (warp-uniform)
+    // the warps of one SM in crit_stride start with the scan for near-critical
+    // rays, the others with the bulk (so that an SM runs the double-float code
+    // or the FP32 code, not both, and its instruction cache holds one of them);
+    // a warp whose queue is drained and whose lanes are all written takes the
+    // other queue, until both are drained (warp-uniform)
     const float band = (float)sol.crit_band;
     const bool use_crit = MIX && band > 0.0f;
-    bool crit_phase = use_crit && ((((blockIdx.x * blockDim.x + threadIdx.x) >> 5) % tp.crit_stride) == 0);
+    unsigned smid = 0;
+    if (use_crit) asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+    bool crit_phase = use_crit && (smid % (unsigned)tp.crit_stride) == 0;
     bool drained_c = !use_crit;
     int wait64 = 0;
     unsigned iter = 0;

@@ -63,9 +63,8 @@ class Scene:
     refine: int = REFINE_HENON
     method: int = DOPRI5              # integrator (Verlet: fixed step h0 > 0)
     fp64_radius_factor: float = 0.0   # mixed paths, double-float on a table: extended-precision steps below
-                                      # factor * r_h (0: 2, < 0: none)
-    fp64_pole_sin: float = 0.0        # the same, where sin(theta) < this (0: 0.3 mixed, none on the prescribed
-                                      # split and on a table; < 0: none)
+                                      # factor * r_h (0: 1.5 mixed, 2 on a table; < 0: none)
+    fp64_pole_sin: float = 0.0        # the same, where sin(theta) < this (0 or < 0: none)
     critical_band: float = 0.0        # mixed paths: rays this close to the critical curve (units of M) are traced
                                       # in double-float (0: 0.1, none on the prescribed split; < 0: none)
     critical_rtol: float = 0.0        # their rtol = atol (0: 1e-10)

@@ -41,8 +41,8 @@ def test_struct_layouts_match_header(tmp_path):
 int main(void) {
   printf("%zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(tt_metric), sizeof(tt_observer), sizeof(tt_camera),
          sizeof(tt_solver), sizeof(tt_disk), sizeof(tt_outputs), sizeof(tt_tune), sizeof(tt_image));
-  printf("%zu %zu %zu\\n", offsetof(tt_solver, fp64_radius_factor), offsetof(tt_camera, pix_count),
-         offsetof(tt_image, out));
+  printf("%zu %zu %zu %zu %zu\\n", offsetof(tt_solver, fp64_radius_factor), offsetof(tt_camera, pix_count),
+         offsetof(tt_image, out), offsetof(tt_solver, critical_rtol), offsetof(tt_tune, crit_refill));
   return 0;
 }
 """)
@@ -53,7 +53,8 @@ int main(void) {
     assert sizes == [C.sizeof(s) for s in (T.TTMetric, T.TTObserver, T.TTCamera, T.TTSolver, T.TTDisk,
                                            T.TTOutputs, T.TTTune, T.TTImage)]
     offs = [int(x) for x in lines[1].split()]
-    assert offs == [T.TTSolver.fp64_radius_factor.offset, T.TTCamera.pix_count.offset, T.TTImage.out.offset]
+    assert offs == [T.TTSolver.fp64_radius_factor.offset, T.TTCamera.pix_count.offset, T.TTImage.out.offset,
+                    T.TTSolver.critical_rtol.offset, T.TTTune.crit_refill.offset]
 
 
 def _args(sc, **over):

@@ -3,10 +3,11 @@ thin-disk scene, at the mixed path's bars: termination codes equal outside the
 +-1e-6 M band around the critical curve; crossing counts equal except there
 or at a disk edge; the radius and g factor of EVERY crossing of every other
 pixel within 1e-5 relative; |H| <= 1e-6 on every escaped ray (evaluated in
-FP64 by the kernel) with the default extended-precision zones (within 2 r_+ of
-the hole and asin(0.3) of the axis) -- on every pixel at 256^2, on the
-benchmark's 2048^2 image (a seeded sample plus its photon-ring pixels) and on
-images of the 64-image batch.
+FP64 by the kernel) with the default extended-precision zone (within 1.5 r_+
+of the hole) -- on every pixel at 256^2, on the benchmark's 2048^2 image (a
+seeded sample plus its photon-ring pixels) and on images of the 64-image
+batch.  The FP32 stages take theta relative to the nearest axis crossing, so
+no polar zone is needed.
 
 Photon-ring crossings (rays that circle the unstable photon orbits) amplify any
 perturbation by ~e^pi per circuit, FP32 stage rounding included: rays within
@@ -66,9 +67,9 @@ def test_mixed_against_oracle(T, orc, ref256, precision, fp64_factor, refine):
     if fp64_factor == 0.0:
         assert got["h_max"][esc].max() <= 1e-6
     else:
-        # without the horizon zone a few escaped rays that passed near r_+ drift further
-        assert np.percentile(got["h_max"][esc], 99.9) <= 1e-6
-        assert got["h_max"][esc].max() <= 5e-6
+        # without the horizon zone: escaped rays never entered it; captured rays
+        # end with a larger |H| (~5e-3 against ~1e-3)
+        assert got["h_max"][esc].max() <= 1e-6
 
 
 def test_without_escalation_photon_rings_drift(T, orc, ref256):
@@ -134,9 +135,9 @@ def test_mixed_batch(T, orc):
 
 def test_prescribed_split(T, orc, ref256):
     """TT_MIXED_SPLIT: FP32 stages with the FP64 state accumulation, error norm,
-    step control, steps below 1.5 r_+ and crossing refinement.  Codes and primary
-    crossings meet the bars; its photon-ring crossings need the escalation too,
-    and without a polar zone rays passing near the axis drift past |H| = 1e-6."""
+    step control, steps below 1.5 r_+ and crossing refinement.  Codes, primary
+    crossings and |H| meet the bars; its photon-ring crossings need the
+    near-critical escalation too."""
     base, ref = ref256
     got = run(T, mixed(base, scenes.MIXED_SPLIT))
     ok = (got["code"] == ref["code"]) & (got["n_cross"] == ref["n_cross"])
@@ -147,7 +148,7 @@ def test_prescribed_split(T, orc, ref256):
     print("prescribed split: r max per order %s, |H| esc max %.2e p99 %.2e" % (
         er.max(axis=1), got["h_max"][esc].max(), np.percentile(got["h_max"][esc], 99)))
     assert er[0].max() <= 1e-5
-    assert np.percentile(got["h_max"][esc], 99) <= 1e-6
+    assert got["h_max"][esc].max() <= 1e-6
     # with the near-critical rays in double-float, every crossing meets the bar
     esc_run = run(T, mixed(base, scenes.MIXED_SPLIT, critical_band=0.1))
     rep = parity.compare_mixed(orc, base, esc_run, ref, np.arange(base.npix))
