@@ -15,18 +15,31 @@ namespace tt {
 
 constexpr double kHalfPi = 1.5707963267948966;   // binary64 pi/2
 
+// Comparisons of doubles on the integer pipe (the FP64 pipe is the FP64
+// path's bound, and a comparison there costs an issue slot like an FMA):
+// IEEE-754 orders non-negative doubles as their bit patterns read as signed
+// 64-bit integers, and every negative double reads as a negative integer, so
+// x < y (x <= y) for y >= 0 and any non-NaN x is the integer comparison.
+__device__ __forceinline__ bool lt_pos(double x, double y) { return __double_as_longlong(x) < __double_as_longlong(y); }
+__device__ __forceinline__ bool le_pos(double x, double y) { return __double_as_longlong(x) <= __double_as_longlong(y); }
+// |x| below a threshold given by the high 32 bits of a positive double.
+__device__ __forceinline__ bool abs_below_hi(double x, int hi) { return (__double2hiint(x) & 0x7fffffff) < hi; }
+constexpr int kHi0p01 = 0x3F847AE1;    // high word of 0.01 (the threshold is 0.01 - 3e-11)
+constexpr int kHi0p1 = 0x3FB99999;     // high word of 0.1 (the threshold is 0.1 - 4e-10)
+
 // ---------------------------------------------------------------------------
-// Reciprocal: the SFU's approximate double reciprocal refined by two Newton-
-// Raphson steps y <- y (2 - x y); each step squares the relative error, so the
-// result is within about one ulp of 1/x for normal x.
+// Reciprocal: the SFU's approximate double reciprocal y refined by one step of
+// the third-order (Halley-type) iteration y <- y (1 + e + e^2), e = 1 - x y:
+// the result is (1/x)(1 - e^3), so the approximation's relative error cubes
+// (two Newton-Raphson steps square it twice; this takes three fused
+// multiply-adds instead of four) and it is within about one ulp of 1/x for
+// normal x.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ double rcp64(double x) {
     double y;
     asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
-    double e = fma(-x, y, 1.0);
-    y = fma(y, e, y);
-    e = fma(-x, y, 1.0);
-    return fma(y, e, y);
+    const double e = fma(-x, y, 1.0);
+    return fma(y, fma(e, e, e), y);
 }
 
 // Per-ray constants of the (time-reversed) photon.
@@ -98,8 +111,9 @@ __device__ __forceinline__ void kerr_flow64_sc(const KerrK& k, const RayConst& R
     const double A = fma(fma(r, r, k.a2), R.pt, R.apph);
     const double SD = Sig * Del;
     const double inv = rcp64(SD * s2);
-    const double iS = inv * (Del * s2);              // 1 / Sigma
-    const double iD = inv * (Sig * s2);              // 1 / Delta
+    const double w = inv * s2;                       // 1 / (Sigma Delta)
+    const double iS = w * Del;                       // 1 / Sigma
+    const double iD = w * Sig;                       // 1 / Delta
     const double u = inv * SD;                       // 1 / sin^2
     const double pr2 = y.pr * y.pr;
     const double AiD = A * iD;
@@ -130,10 +144,18 @@ __device__ __forceinline__ void kerr_flow64(const KerrK& k, const RayConst& R, c
 // sin and cos of theta from those of a nearby theta0 (the start of the step):
 // angle addition with the Taylor series of d = theta - theta0 through d^9 and
 // d^8, whose truncation is below 3e-18 for |d| < 0.1 -- ~20 FP64 instructions
-// against ~28 for a full sincos (measured on GB300); farther away, sincos.
+// against ~28 for a full sincos (measured on GB300); through d^5 and d^6 for
+// |d| < 0.01 (truncation below 2e-18, three fused multiply-adds fewer); farther
+// away, sincos.  (The tier thresholds are compared on the integer pipe.)
 __device__ __forceinline__ void sincos_near(double th, double th0, double s0, double c0, double& s, double& c) {
     const double d = th - th0;
-    if (fabs(d) < 0.1) {
+    if (abs_below_hi(d, kHi0p01)) {
+        const double d2 = d * d;
+        const double sd = d * fma(d2, fma(d2, 1.0 / 120.0, -1.0 / 6.0), 1.0);
+        const double cd = fma(d2, fma(d2, fma(d2, -1.0 / 720.0, 1.0 / 24.0), -0.5), 1.0);
+        s = fma(s0, cd, c0 * sd);
+        c = fma(c0, cd, -(s0 * sd));
+    } else if (abs_below_hi(d, kHi0p1)) {
         const double d2 = d * d;
         const double sd =
             d * fma(d2, fma(d2, fma(d2, fma(d2, 1.0 / 362880.0, -1.0 / 5040.0), 1.0 / 120.0), -1.0 / 6.0), 1.0);

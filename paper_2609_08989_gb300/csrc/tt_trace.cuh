@@ -46,7 +46,7 @@ __device__ __forceinline__ double pow_m01(double x) {
 
 // Step-size factor 0.9 err^(-1/5) from err^2 (large when err^2 is tiny or 0).
 __device__ __forceinline__ double step_factor(double err2) {
-    return (err2 < 1e-30) ? 1e30 : 0.9 * pow_m01(err2);
+    return lt_pos(err2, 1e-30) ? 1e30 : 0.9 * pow_m01(err2);
 }
 
 // ---------------------------------------------------------------------------
@@ -283,7 +283,9 @@ __device__ __forceinline__ double err_norm2(const State& y, const State& yn, con
     const double s3 = fma(rtol, fmax(fabs(y.pth), fabs(yn.pth)), atol);
     const double p01 = s0 * s1, p23 = s2 * s3;
     const double pp = p01 * p23;
-    if (!(pp > 1e-280 && pp < 1e280)) {
+    // outside [2^-930, 2^930] (the exponent field, on the integer pipe)
+    const int ex = (__double2hiint(pp) >> 20) & 0x7ff;
+    if (ex < 1023 - 930 || ex > 1023 + 930) {
         const double q3 = err_ratio(e.pth, y.pth, yn.pth, atol, rtol);
         return 0.25 * fma(q3, q3, sq3(err_ratio(e.r, y.r, yn.r, atol, rtol), err_ratio(e.th, y.th, yn.th, atol, rtol),
                                       err_ratio(e.pr, y.pr, yn.pr, atol, rtol)));
@@ -895,7 +897,7 @@ __device__ int step_ray64(Lane& L, const SolverDesc& sol) {
     const ImageDesc& d = *L.d;
     if ((long long)L.steps + (long long)L.rejects >= sol.max_steps) return 2;
     const double hmin = (sol.h_min > 0.0) ? sol.h_min : 1e-14 * fmax(1.0, fabs(L.lam));
-    if (L.h < hmin) return 3;
+    if (lt_pos(L.h, hmin)) return 3;
     State yn, kn, e;
     double Hn, sn = L.s0, cn = L.c0;
     if constexpr (METHOD == 4) {
@@ -910,9 +912,9 @@ __device__ int step_ray64(Lane& L, const SolverDesc& sol) {
     if (nan_bits(err2) | nonfinite_bits(yn.r) | nonfinite_bits(yn.th) | nonfinite_bits(yn.pr) |
         nonfinite_bits(yn.pth))
         return 4;
-    if (err2 <= 1.0) {
+    if (le_pos(err2, 1.0)) {
         L.steps++;
-        if (d.disk && ((L.y.th <= kHalfPi) != (yn.th <= kHalfPi))) {
+        if (d.disk && (le_pos(L.y.th, kHalfPi) != le_pos(yn.th, kHalfPi))) {
             if (sol.refine == 1) {
                 const double rc = refine_hermite64(L.y, L.k1, yn, kn, L.h);
                 if (L.pend) refine_pending<METRIC, PREC, METHOD>(L, sol);
@@ -927,8 +929,8 @@ __device__ int step_ray64(Lane& L, const SolverDesc& sol) {
         L.s0 = sn;
         L.c0 = cn;
         L.hmax = fmax(L.hmax, fabs(Hn));
-        if (yn.r < d.r_capture) return 1;
-        if (yn.r > d.r_escape) return 0;
+        if (lt_pos(yn.r, d.r_capture)) return 1;
+        if (lt_pos(d.r_escape, yn.r)) return 0;
         if constexpr (METHOD == 3) {
             L.h *= fmin(L.last_rej ? 1.0 : 4.0, fmax(0.02, gbs_factor(err2)));
         } else if constexpr (METHOD != 4) {
