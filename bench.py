@@ -48,9 +48,9 @@ FP32_PEAK_DERIVED = SM_COUNT * SM_MAX_MHZ * 1e6 * 128 * 2 / 1e12
 # counted from the kernel source of this build (FMA = 2; add, mul, reciprocal and
 # sqrt 1 each, the reciprocal's Newton refinement not counted; sin and cos 1 each,
 # however they are evaluated -- here by angle addition from the step start):
-# 6 flow evaluations x 56 + stage combinations 226 (stages 2-4 with h-scaled
+# 6 flow evaluations x 55 + stage combinations 226 (stages 2-4 with h-scaled
 # coefficients) + error norm 30 (one shared reciprocal) + step control 5.
-FLOW_FLOPS, NORM_FLOPS, CONTROL_FLOPS = 56, 30, 5
+FLOW_FLOPS, NORM_FLOPS, CONTROL_FLOPS = 55, 30, 5
 FLOPS_PER_STEP = 6 * FLOW_FLOPS + 226 + NORM_FLOPS + CONTROL_FLOPS
 # Cash-Karp and Fehlberg also evaluate the flow six times per step attempt (five
 # stages and the new point); their stage sums have one (Fehlberg: e_7 = 0) or two
@@ -82,8 +82,9 @@ BYTES_OUT_PER_PIXEL = 3 * 3 * 8 + 8 + 8 + 4 + 4 + 1 + 1
 # dram__bytes_read.sum + dram__bytes_write.sum of one full-size launch (None: not
 # captured for this build of the kernel)
 TRAFFIC_BYTES_1024 = None
-# host-to-device input of one step: the image descriptor (sizeof(tt::ImageDesc)) and the queue reset
-DESC_BYTES = 384 + 16
+# host-to-device input of one step: the launch's parameter block (sizeof(tt::LaunchParams<1>):
+# solver settings, launch shape and the image descriptor)
+DESC_BYTES = 728
 # The tolerance of the equal-accuracy comparison: the mixed paths' own, at which the FP64
 # and double-float paths also keep |H| <= 1e-6 on every escaped ray of the 2048^2 disk
 # image (the next looser ones measured there, 2e-8 and 3e-8, give 1.1e-6 and more) and

@@ -343,6 +343,14 @@ const char *tartarus_error_string(int status);
 /* Number of kernels this library has launched in this process. */
 long long tartarus_launch_count(void);
 
+/* Bounds-checking build only (the library compiled with TT_BOUNDS_CHECK, a
+ * test artefact): every output store of the kernels is checked against its
+ * buffer's length, and a store that would fall outside is skipped and counted
+ * instead (no trap, no fault).  Synchronises the device, writes the number of
+ * such stores since the last call to *count and resets it.  The ordinary
+ * build writes 0 and returns TT_EUNSUPPORTED.  TT_EINVAL if count is NULL. */
+int tartarus_debug_faults(long long *count);
+
 /* Version string. */
 const char *tartarus_version(void);
 

@@ -17,6 +17,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 SO = os.path.join(BUILD, "libtartarus.so")
+DEBUG_BUILD = os.path.join(BUILD, "bounds_check")
+DEBUG_SO = os.path.join(BUILD, "libtartarus_debug.so")
 PEAKS_SRC = "tt_peaks.cu"
 PEAKS_SO = os.path.join(BUILD, "libtt_peaks.so")
 SOURCES = ["tt_capi.cu", "tt_kernel64.cu", "tt_kernel_mixed.cu", "tt_kernel_split.cu", "tt_kernel_ck.cu", "tt_kernel_f.cu",
@@ -65,14 +67,26 @@ def build(force: bool = False, verbose: bool = False) -> str:
     return so
 
 
-def _build_tracer(force: bool, verbose: bool) -> str:
-    if not force and os.path.exists(SO) and os.path.getmtime(SO) >= _newest_input():
-        return SO
+def build_debug(force: bool = False) -> str:
+    """The bounds-checking build (TT_BOUNDS_CHECK: every output store checked
+    and an out-of-range one counted): libtartarus_debug.so, a test artefact
+    compiled on demand."""
+    return _build_tracer(force, False, debug=True)
+
+
+def _build_tracer(force: bool, verbose: bool, debug: bool = False) -> str:
+    so = DEBUG_SO if debug else SO
+    odir = DEBUG_BUILD if debug else BUILD
+    os.makedirs(odir, exist_ok=True)
+    if not force and os.path.exists(so) and os.path.getmtime(so) >= _newest_input():
+        return so
     objs = []
 
     def compile_one(src):
-        obj = os.path.join(BUILD, src.replace(".cu", ".o"))
+        obj = os.path.join(odir, src.replace(".cu", ".o"))
         extra = ["-fmad=false"] if src in NO_CONTRACT else []
+        if debug:
+            extra.append("-DTT_BOUNDS_CHECK")
         cmd = [nvcc(), *ARCH, *FLAGS, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
@@ -85,13 +99,13 @@ def _build_tracer(force: bool, verbose: bool) -> str:
 
     with ThreadPoolExecutor(len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
-    tmp = SO + ".%d.tmp" % os.getpid()
+    tmp = so + ".%d.tmp" % os.getpid()
     cmd = [nvcc(), *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s%s" % (r.stdout, r.stderr))
-    os.replace(tmp, SO)
-    return SO
+    os.replace(tmp, so)
+    return so
 
 
 if __name__ == "__main__":

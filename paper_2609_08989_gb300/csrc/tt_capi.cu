@@ -92,6 +92,26 @@ int check_outputs(const tt_outputs* o) {
     return TT_OK;
 }
 
+#ifdef TT_BOUNDS_CHECK
+// The bounds-checking build's fault counter: a file-scope device variable (no
+// allocation), its address looked up once per device.
+static __device__ unsigned long long tt_fault_count;
+unsigned long long* g_fault_addr[64] = {};
+std::mutex g_fault_mu;
+
+unsigned long long* fault_counter() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lk(g_fault_mu);
+    if (!g_fault_addr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, tt_fault_count) != cudaSuccess) return nullptr;
+        g_fault_addr[dev] = static_cast<unsigned long long*>(p);
+    }
+    return g_fault_addr[dev];
+}
+#endif
+
 // Resolve one image into a kernel descriptor.
 int make_desc(const tt_metric* m, const tt_observer* obs, const tt_camera* cam, const tt_solver* sol,
               const tt_disk* disk, const tt_outputs* out, tt::ImageDesc* d) {
@@ -239,6 +259,11 @@ tt::SolverDesc make_solver(const tt_solver* s) {
     // none on the prescribed split), at the FP64 path's tolerance by default
     sd.crit_band = 0.0;
     sd.crit_rtol = sd.crit_atol = 0.0;
+#ifdef TT_BOUNDS_CHECK
+    sd.faults = fault_counter();
+#else
+    sd.faults = nullptr;
+#endif
     if (mixed_precision(s->precision)) {
         const double band_default = s->precision == TT_MIXED_SPLIT ? -1.0 : 0.1;
         const double band = s->critical_band != 0.0 ? s->critical_band : band_default;
@@ -694,6 +719,29 @@ const char* tartarus_error_string(int status) {
 
 long long tartarus_launch_count(void) { return g_launches.load(); }
 
-const char* tartarus_version(void) { return "tartarus-gb300 0.1 (sm_103a)"; }
+int tartarus_debug_faults(long long* count) {
+    if (!count) return TT_EINVAL;
+#ifdef TT_BOUNDS_CHECK
+    unsigned long long* p = fault_counter();
+    if (!p) return TT_ECUDA;
+    unsigned long long v = 0;
+    if (cudaDeviceSynchronize() != cudaSuccess) return TT_ECUDA;
+    if (cudaMemcpy(&v, p, sizeof v, cudaMemcpyDeviceToHost) != cudaSuccess) return TT_ECUDA;
+    if (cudaMemset(p, 0, sizeof v) != cudaSuccess) return TT_ECUDA;
+    *count = (long long)v;
+    return TT_OK;
+#else
+    *count = 0;
+    return TT_EUNSUPPORTED;
+#endif
+}
+
+const char* tartarus_version(void) {
+#ifdef TT_BOUNDS_CHECK
+    return "tartarus-gb300 0.2 (sm_103a, bounds-checking build)";
+#else
+    return "tartarus-gb300 0.2 (sm_103a)";
+#endif
+}
 
 }  // extern "C"

@@ -74,6 +74,9 @@ struct SolverDesc {
     // mixed paths: rays within crit_band (units of M) of the critical curve are
     // traced in double-float at crit_rtol / crit_atol (0: none)
     double crit_band, crit_rtol, crit_atol;
+    // bounds-checking build (TT_BOUNDS_CHECK): counter of output stores whose
+    // index fell outside their buffer (skipped, never made); unused otherwise
+    unsigned long long* faults;
 };
 
 struct LaunchShape {

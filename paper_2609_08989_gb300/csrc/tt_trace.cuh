@@ -511,19 +511,34 @@ struct Lane {
     bool crit;
 };
 
-__device__ __forceinline__ void write_final(const Lane& L, int code) {
+// Output stores.  The bounds-checking build (TT_BOUNDS_CHECK) tests every index
+// against its buffer's length and, instead of a store outside it, counts a
+// fault in the solver's counter (read back by tartarus_debug_faults); nothing
+// traps.  Otherwise the plain store.
+#ifdef TT_BOUNDS_CHECK
+#define TT_STORE(d, arr, idx, len, val)                                        \
+    do {                                                                       \
+        const long long i_ = (idx);                                            \
+        if (i_ >= 0 && i_ < (len)) (d).arr[i_] = (val);                        \
+        else if (sol.faults) atomicAdd(sol.faults, 1ull);                      \
+    } while (0)
+#else
+#define TT_STORE(d, arr, idx, len, val) ((d).arr[(idx)] = (val))
+#endif
+
+__device__ __forceinline__ void write_final(const Lane& L, int code, const SolverDesc& sol) {
     const ImageDesc& d = *L.d;
     const long long q = L.q, n = d.pix_count;
-    d.code[q] = (int8_t)code;
-    d.n_cross[q] = (int8_t)min(L.ncross, 127);
-    d.intensity[q] = L.inten;
-    d.h_max[q] = fmax(L.hmax, (double)L.hmaxf);
-    d.steps[q] = L.steps;
-    d.rejects[q] = L.rejects;
+    TT_STORE(d, code, q, n, (int8_t)code);
+    TT_STORE(d, n_cross, q, n, (int8_t)min(L.ncross, 127));
+    TT_STORE(d, intensity, q, n, L.inten);
+    TT_STORE(d, h_max, q, n, fmax(L.hmax, (double)L.hmaxf));
+    TT_STORE(d, steps, q, n, L.steps);
+    TT_STORE(d, rejects, q, n, L.rejects);
     for (int k = L.nrec; k < kMaxCross; ++k) {
-        d.r_cross[k * n + q] = 0.0;
-        d.g[k * n + q] = 0.0;
-        d.I_cross[k * n + q] = 0.0;
+        TT_STORE(d, r_cross, k * n + q, kMaxCross * n, 0.0);
+        TT_STORE(d, g, k * n + q, kMaxCross * n, 0.0);
+        TT_STORE(d, I_cross, k * n + q, kMaxCross * n, 0.0);
     }
 }
 
@@ -663,7 +678,7 @@ __device__ bool init_ray(Lane& L, const ImageDesc* d_ptr, long long q, const Sol
     const double D = d.r_obs, th = d.theta_obs;
     const double rho2 = alpha * alpha + beta * beta;
     if (!isfinite(alpha) || !isfinite(beta) || !(rho2 < D * D)) {
-        write_final(L, 5);
+        write_final(L, 5, sol);
         return false;
     }
     // ZAMO tetrad at the observer: e_(t) = (1/N)(dt + omega dphi), e_(i) = d_i / sqrt(g_ii)
@@ -752,7 +767,7 @@ __device__ bool init_ray(Lane& L, const ImageDesc* d_ptr, long long q, const Sol
 // Emission at a refined crossing radius (paper Sec. 2.3-2.4): counted if on the
 // disk, stored (r, g, g^4 F) while slots remain.
 template <int METRIC>
-__device__ __forceinline__ void record_crossing(Lane& L, double rc) {
+__device__ __forceinline__ void record_crossing(Lane& L, double rc, const SolverDesc& sol) {
     const ImageDesc& d = *L.d;
     if (rc >= d.r_in && rc <= d.r_out) {
         if (L.nrec < d.max_cross) {
@@ -761,9 +776,9 @@ __device__ __forceinline__ void record_crossing(Lane& L, double rc) {
             const double g2 = gf * gf;
             const double I = g2 * g2 * F;
             const long long n = d.pix_count, q = L.q;
-            d.r_cross[L.nrec * n + q] = rc;
-            d.g[L.nrec * n + q] = gf;
-            d.I_cross[L.nrec * n + q] = I;
+            TT_STORE(d, r_cross, L.nrec * n + q, kMaxCross * n, rc);
+            TT_STORE(d, g, L.nrec * n + q, kMaxCross * n, gf);
+            TT_STORE(d, I_cross, L.nrec * n + q, kMaxCross * n, I);
             L.inten += I;
             L.nrec++;
         }
@@ -878,7 +893,7 @@ __device__ void refine_pending(Lane& L, const SolverDesc& sol) {
         else
             rc = refine_henon64<METRIC, (METHOD <= 2 ? METHOD : 0)>(d, L.kk, L.R, L.yc, f0, sol.atol, sol.rtol);
     }
-    record_crossing<METRIC>(L, rc);
+    record_crossing<METRIC>(L, rc, sol);
     L.pend = false;
 }
 
@@ -918,7 +933,7 @@ __device__ int step_ray64(Lane& L, const SolverDesc& sol) {
             if (sol.refine == 1) {
                 const double rc = refine_hermite64(L.y, L.k1, yn, kn, L.h);
                 if (L.pend) refine_pending<METRIC, PREC, METHOD>(L, sol);
-                record_crossing<METRIC>(L, rc);
+                record_crossing<METRIC>(L, rc, sol);
             } else {
                 note_crossing<METRIC, PREC, METHOD>(L, L.y, sol);
             }
@@ -1444,7 +1459,7 @@ __device__ __forceinline__ void trace_loop(const ImageDesc* descs, int n_desc, l
             if (st != kIdle && L.pend) refine();
             if (st == kDone) {
                 if (MIX && !L.crit) check_h64<ACC>(L, yhi);
-                write_final(L, L.code);
+                write_final(L, L.code, sol);
                 st = kIdle;
             }
             if (crit_phase) {

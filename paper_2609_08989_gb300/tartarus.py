@@ -23,7 +23,7 @@ TABLE_NF = 20
 
 EXPORTS = ["tartarus_trace", "tartarus_trace_host", "tartarus_trace_batch", "tartarus_trace_batch_noalloc",
            "tartarus_table_create", "tartarus_table_destroy", "tartarus_table_coefficients",
-           "tartarus_error_string", "tartarus_launch_count", "tartarus_version"]
+           "tartarus_error_string", "tartarus_launch_count", "tartarus_debug_faults", "tartarus_version"]
 
 
 class TTMetric(C.Structure):
@@ -82,8 +82,32 @@ class TartarusError(RuntimeError):
         self.status = status
 
 
+_bounds_check = False
+
+
 def library_path() -> str:
-    return _build.SO
+    return _build.DEBUG_SO if _bounds_check else _build.SO
+
+
+def use_bounds_check_build(enable: bool = True) -> None:
+    """Route every entry point to the bounds-checking build of the library
+    (libtartarus_debug.so, compiled with TT_BOUNDS_CHECK: every output store is
+    checked and an out-of-range one counted, see bounds_faults).  A test
+    artefact; takes effect before the first call that loads the library."""
+    global _bounds_check, _lib
+    with _lock:
+        if _lib is not None and enable != _bounds_check:
+            raise RuntimeError("the library is already loaded; choose the build before the first call")
+        _bounds_check = enable
+
+
+def bounds_faults() -> int:
+    """tartarus_debug_faults: out-of-range output stores since the last call
+    (bounds-checking build only)."""
+    n = C.c_longlong()
+    st = lib().tartarus_debug_faults(C.byref(n))
+    _check(st, "tartarus_debug_faults")
+    return n.value
 
 
 def lib():
@@ -91,7 +115,7 @@ def lib():
     global _lib
     with _lock:
         if _lib is None:
-            path = _build.build()
+            path = _build.build_debug() if _bounds_check else _build.build()
             if not os.path.exists(path):
                 raise RuntimeError("libtartarus.so is not built: run paper_2609_08989_gb300._build.build()")
             L = C.CDLL(path)
@@ -119,6 +143,8 @@ def lib():
             L.tartarus_error_string.restype = C.c_char_p
             L.tartarus_launch_count.argtypes = []
             L.tartarus_launch_count.restype = C.c_longlong
+            L.tartarus_debug_faults.argtypes = [P(C.c_longlong)]
+            L.tartarus_debug_faults.restype = C.c_int
             L.tartarus_version.argtypes = []
             L.tartarus_version.restype = C.c_char_p
             _lib = L
