@@ -174,6 +174,15 @@ def config_dict(sc, world, shard=False):
             "l2": "flushed between timed steps (256 MiB write); working set is a few MB of state + outputs"}
 
 
+def kernel_name(sc):
+    """The tracing kernel the FP64 launch of this scene runs (its tuned block size)."""
+    from paper_2609_08989_gb300 import autotune
+    block = (autotune.cached(sc) or {}).get("block", 0)
+    if sc.method == 0:
+        return {256: "trace_kernel64_b256<0,1>", 384: "trace_kernel64_b384<0,1>"}.get(block, "trace_kernel64<0,1>")
+    return "trace_kernel_rk<%d,0,1,%d>" % (sc.method, 256 if block in (256, 384) else 128)
+
+
 def h_stats(out):
     """|H| maxima of escaped and captured rays of a device output dict."""
     import numpy as np
@@ -575,8 +584,7 @@ def run_tartarus(args):
                          "traffic": (TRAFFIC_BYTES_1024 * count / (1024 * 1024)
                                      if TRAFFIC_BYTES_1024 and args.precision == "fp64" and sc.method == 0 else None),
                          "traffic_note": "DRAM bytes of one full-size launch (ncu), scaled by the pixels traced",
-                         "kernel": ("trace_kernel64_b256<0,1>" if sc.method == 0
-                                    else "trace_kernel_rk<%d,0,1,256>" % sc.method), "kernel_ms": mean_kern,
+                         "kernel": kernel_name(sc), "kernel_ms": mean_kern,
                          "flops_per_unit": fpu,
                          "unit_of_work": "%s step attempt" % METHOD_NAMES[sc.method],
                          "issued": ({"fp64_flops_per_unit": issued,

@@ -222,14 +222,13 @@ typedef struct {
  *                   128 threads, single camera: 0 the compiler's choice, 1 at
  *                   most 168, 2 at most 128 (other kernels ignore it)
  *   refill          flush finished rays and refill lanes once at least this many
- *                   lanes of a warp are done or idle (1..32; default 4 on the
- *                   FP64 paths, 16 on the mixed paths)
+ *                   lanes of a warp are done or idle (1..32; default 32)
  *   blocks_per_sm   persistent blocks per SM (0: as many as fit)
  *   crossing_batch  refine disk crossings once this many lanes of a warp have
- *                   one pending (1..32; default 8 FP64, 16 mixed)
+ *                   one pending (1..32; default 16 FP64, 32 otherwise)
  *   fp64_batch      mixed paths (and the double-float path on a table): run the
  *                   extended-precision zone steps once this many lanes need one
- *                   (1..32, default 16; 1 on the double-float path)
+ *                   (1..32, default 32; 1 on the double-float path)
  *   monitor_period  mixed paths: evaluate |H| in FP64 every this many warp
  *                   iterations (default 32)
  *   fp64_wait       mixed paths: lanes waiting for a zone step get one after at

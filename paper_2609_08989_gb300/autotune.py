@@ -34,18 +34,25 @@ SPACE: Dict[str, Dict[str, List[int]]] = {
              "crossing_batch": [2, 4, 8, 16, 24, 32], "blocks_per_sm": [0, 1, 2]},
     "table": {"refill": [1, 2, 4, 8, 16], "crossing_batch": [2, 4, 8, 16, 24], "blocks_per_sm": [0, 1, 2]},
     "mixed": {"refill": [8, 16, 24, 32], "crossing_batch": [8, 16, 24, 32], "fp64_batch": [8, 16, 24, 32],
-              "fp64_wait": [64, 256, 1024], "monitor_period": [16, 32, 64], "blocks_per_sm": [0, 1, 2]},
+              "fp64_wait": [64, 256, 1024], "monitor_period": [16, 32, 64], "blocks_per_sm": [0, 1, 2],
+              "crit_stride": [1, 2, 4], "crit_refill": [8, 16, 32]},
 }
 SPACE["mixed_pair"] = SPACE["mixed"]
 SPACE["mixed_split"] = SPACE["mixed"]
+SPACE["mixed_pair_batch"] = SPACE["mixed"]
 SPACE["double_float"] = {"refill": [2, 4, 8, 16, 32], "crossing_batch": [4, 8, 16, 32], "blocks_per_sm": [0, 1, 2]}
 SPACE["table_double_float"] = {"refill": [2, 4, 8, 16, 32], "crossing_batch": [4, 8, 16, 32], "fp64_batch": [1, 4, 16]}
 
 
-def workload_class(sc) -> str:
+def workload_class(sc, batch: bool = False) -> str:
+    """The class of a scene; batch: one of several images traced in one launch
+    (the mixed-pair batch has a class of its own, its images being uneven)."""
     if sc.metric_kind == 1:
         return "table_double_float" if sc.precision == 3 else "table"
-    return {0: "fp64", 1: "mixed", 2: "mixed_pair", 3: "double_float", 4: "mixed_split"}[sc.precision]
+    cls = {0: "fp64", 1: "mixed", 2: "mixed_pair", 3: "double_float", 4: "mixed_split"}[sc.precision]
+    if batch and cls == "mixed_pair":
+        return "mixed_pair_batch"
+    return cls
 
 
 def _device_key() -> str:
@@ -65,13 +72,15 @@ def load() -> dict:
         return _cache
 
 
-def cached(sc) -> Optional[dict]:
+def cached(sc, batch: bool = False) -> Optional[dict]:
     """The tuned shape for this scene's class on the current device, or None."""
     try:
         dev = _device_key()
     except Exception:
         return None
-    entry = load().get(dev, {}).get(workload_class(sc))
+    entry = load().get(dev, {}).get(workload_class(sc, batch))
+    if entry is None and batch:
+        entry = load().get(dev, {}).get(workload_class(sc))
     return dict(entry["tune"]) if entry else None
 
 
@@ -135,6 +144,22 @@ def tune_scene(sc, reps: int = 2, sweeps: int = 2, save: bool = True, log=None) 
     return best, ms
 
 
+def tune_batch(imgs, reps: int = 2, sweeps: int = 2, save: bool = True, log=None) -> Tuple[dict, float]:
+    """Tune the launch shape of one batch call over ``imgs`` (closed-form Kerr)."""
+    from . import tartarus as T
+    outs = [T.alloc_outputs(s.npix) for s in imgs]
+    cls = workload_class(imgs[0], batch=True)
+
+    def run(tune):
+        T.trace_batch(imgs, outs, tune=tune)
+
+    base_ms = _time(run, {}, reps)
+    best, ms, _ = search(run, SPACE[cls], reps=reps, sweeps=sweeps, log=log)
+    if save:
+        record(cls, best, ms, base_ms, "batch_uneven_%d_images" % len(imgs))
+    return best, ms
+
+
 def record(cls: str, tune: dict, ms: float, base_ms: float, workload: str) -> None:
     data = load()
     dev = _device_key()
@@ -153,10 +178,14 @@ if __name__ == "__main__":
     todo = {"fp64": lambda: scenes.kerr_disk(1024),
             "mixed": lambda: scenes.kerr_disk_mixed(2048),
             "mixed_pair": lambda: scenes.kerr_disk_mixed(2048).replace(precision=scenes.MIXED_PAIR),
+            "mixed_split": lambda: scenes.kerr_disk_mixed(2048).replace(precision=scenes.MIXED_SPLIT),
             "double_float": lambda: scenes.kerr_disk(1024).replace(precision=scenes.DOUBLE_FLOAT),
             "table": lambda: scenes.table_kerr_with_nodes(1024),
-            "table_double_float": lambda: scenes.table_kerr_with_nodes(1024).replace(precision=scenes.DOUBLE_FLOAT)}
+            "table_double_float": lambda: scenes.table_kerr_with_nodes(2048).replace(precision=scenes.DOUBLE_FLOAT)}
     for name in which:
-        sc = todo[name]()
-        best, ms = tune_scene(sc, log=lambda m: print("  " + m, flush=True))
+        if name == "mixed_pair_batch":
+            best, ms = tune_batch(scenes.batch_uneven(64, seed=2609, precision=scenes.MIXED_PAIR),
+                                  log=lambda m: print("  " + m, flush=True))
+        else:
+            best, ms = tune_scene(todo[name](), log=lambda m: print("  " + m, flush=True))
         print("%s: %s  %.2f ms" % (name, best, ms), flush=True)

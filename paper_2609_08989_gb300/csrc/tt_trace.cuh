@@ -1647,13 +1647,15 @@ void fill_params(LaunchParams<N>& p, const ImageDesc* descs, int n, long long to
     p.solc.rtol = sol.crit_rtol;
     p.solc.atol = sol.crit_atol;
     p.n_desc = n;
-    // defaults: the FP64 path steps every lane in FP64 anyway, so it refills and
-    // refines in small batches; the mixed paths batch their FP64 work harder
+    // defaults (the autotuner's choices on GB300): refill once every lane of the
+    // warp is free (initial data and the final record then run with full lanes),
+    // refine crossings in batches of 16 (FP64) or 32 lanes, and run the mixed
+    // paths' zone steps once every running lane needs one (or after fp64_wait)
     const bool mixed = sol.precision != 0;
-    p.tune.refill = shape.refill > 0 ? shape.refill : (mixed ? 16 : 4);
-    p.tune.crossing_batch = shape.crossing_batch > 0 ? shape.crossing_batch : (mixed ? 16 : 8);
+    p.tune.refill = shape.refill > 0 ? shape.refill : 32;
+    p.tune.crossing_batch = shape.crossing_batch > 0 ? shape.crossing_batch : (mixed ? 32 : 16);
     // (the double-float table path's FP64 zone steps measured fastest unbatched)
-    p.tune.fp64_batch = shape.fp64_batch > 0 ? shape.fp64_batch : (sol.precision == 3 ? 1 : 16);
+    p.tune.fp64_batch = shape.fp64_batch > 0 ? shape.fp64_batch : (sol.precision == 3 ? 1 : 32);
     p.tune.monitor_period = shape.monitor_period > 0 ? shape.monitor_period : 32;
     p.tune.fp64_wait = shape.fp64_wait > 0 ? shape.fp64_wait : 64;
     p.tune.crit_stride = shape.crit_stride > 0 ? shape.crit_stride : 1;

@@ -247,12 +247,12 @@ def _disk(sc: Scene) -> TTDisk:
                   max_crossings=sc.max_crossings, doppler=sc.doppler)
 
 
-def _tune(tune, sc: Optional[Scene] = None) -> Optional[TTTune]:
+def _tune(tune, sc: Optional[Scene] = None, batch: bool = False) -> Optional[TTTune]:
     """Explicit shape, else the autotuned shape cached for this device and
     workload class, else the library's built-in defaults (None)."""
     if tune is None and sc is not None:
         from . import autotune
-        tune = autotune.cached(sc)
+        tune = autotune.cached(sc, batch)
     if tune is None:
         return None
     if isinstance(tune, TTTune):
@@ -260,8 +260,8 @@ def _tune(tune, sc: Optional[Scene] = None) -> Optional[TTTune]:
     return TTTune(**{f: int(tune.get(f, 0)) for f, _ in TTTune._fields_})
 
 
-def _tune_ref(tune, sc):
-    t = _tune(tune, sc)
+def _tune_ref(tune, sc, batch: bool = False):
+    t = _tune(tune, sc, batch)
     return C.byref(t) if t is not None else None
 
 
@@ -377,7 +377,7 @@ def trace_batch(scenes: Sequence[Scene], outs=None, stream=None, tune=None,
         imgs[i].out = _out_struct(outs[i])
     status = (C.c_int * max(n, 1))()
     st = lib().tartarus_trace_batch(imgs, n, C.byref(solver_struct(scenes[0])),
-                                    _tune_ref(tune, scenes[0] if n else None), status, _stream_ptr(stream))
+                                    _tune_ref(tune, scenes[0] if n else None, n > 1), status, _stream_ptr(stream))
     if status_out is not None:
         status_out[:] = list(status)[:n]
     if st != TT_OK and status_out is None:
@@ -403,7 +403,7 @@ def trace_batch_noalloc(scenes: Sequence[Scene], outs, stream=None, tune=None,
         imgs[i].out = _out_struct(outs[i])
     status = (C.c_int * max(n, 1))()
     st = lib().tartarus_trace_batch_noalloc(imgs, n, C.byref(solver_struct(scenes[0])),
-                                            _tune_ref(tune, scenes[0] if n else None), status,
+                                            _tune_ref(tune, scenes[0] if n else None, n > 1), status,
                                             _stream_ptr(stream))
     if status_out is not None:
         status_out[:] = list(status)[:n]
