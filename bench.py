@@ -72,16 +72,19 @@ METHOD_NAMES = {v: k for k, v in METHODS.items()}
 # its stages, norm and control as in the FP64 step before the h-scaling above).
 FLOPS_PER_STEP_F32 = 6 * 72 + 232 + 20 + 5
 # FP64 thread instructions per Dormand-Prince step attempt of the FP64 kernel, from ncu's
-# instruction counts on the 512^2 image: DFMA, DMUL, DADD
-FP64_ISSUED_PER_STEP = (281.2, 208.6, 19.5)
+# instruction counts on the 512^2 image (7.02e7 attempts): DFMA, DMUL, DADD
+FP64_ISSUED_PER_STEP = (260.7, 202.6, 19.5)
 # FP32 thread instructions (FFMA + FMUL + FADD) per double-float step attempt, from ncu's
 # instruction counts on the 512^2 image
 DF_FP32_INST_PER_STEP = 4693
+# the same per step attempt of the mixed-pair kernel on the 1024^2 image (its FP32 steps with
+# the zone and near-critical double-float steps amortised over all attempts)
+MIXED_FP32_INST_PER_STEP = 837
 BYTES_OUT_PER_PIXEL = 3 * 3 * 8 + 8 + 8 + 4 + 4 + 1 + 1
 # DRAM traffic of the FP64 tracer per launch on the 1024^2 image: ncu's
-# dram__bytes_read.sum + dram__bytes_write.sum of one full-size launch (None: not
-# captured for this build of the kernel)
-TRAFFIC_BYTES_1024 = None
+# dram__bytes_read.sum + dram__bytes_write.sum of one full-size launch (1.6 MB read,
+# 49.8 MB written: part of the 103 MB of outputs leaves the L2 during the kernel)
+TRAFFIC_BYTES_1024 = 1635840 + 49813504
 # host-to-device input of one step: the launch's parameter block (sizeof(tt::LaunchParams<1>):
 # solver settings, launch shape and the image descriptor)
 DESC_BYTES = 728
@@ -205,8 +208,12 @@ def fp32_roofline(attempts, ms, peaks):
     """Algorithmic FP32 flops of the mixed step over the kernel time, against the
     measured FP32 FMA rate."""
     ach = FLOPS_PER_STEP_F32 * attempts / (ms / 1e3) / 1e12
+    inst = MIXED_FP32_INST_PER_STEP * attempts / (ms / 1e3)
     return {"bound": "alu", "achieved": ach, "peak": peaks["fp32"], "unit": "TFLOP/s",
             "frac": ach / peaks["fp32"], "peak_source": peaks["fp32_source"],
+            "issued": {"fp32_instructions_per_unit": MIXED_FP32_INST_PER_STEP,
+                       "frac_of_fp32_instruction_peak": inst / (peaks["fp32"] / 2 * 1e12),
+                       "source": "FFMA + FMUL + FADD per attempt from ncu's counts (mixed pair, 1024^2)"},
             "peak_derived": FP32_PEAK_DERIVED, "frac_of_derived": ach / FP32_PEAK_DERIVED,
             "flops_per_unit": FLOPS_PER_STEP_F32, "traffic": None,
             "unit_of_work": "step attempt, each counted as one FP32 Dormand-Prince step (the double-float "
@@ -442,7 +449,7 @@ def integrator_objects(T, args, flush, peaks):
     pairs = {}
     for name in ("cash_karp", "fehlberg", "gbs", "verlet"):
         psc = workload(VERLET_N if name == "verlet" else args.n, "fp64", name)
-        ms, pout = time_variant(T, psc, 2, 1, flush)
+        ms, pout = time_variant(T, psc, 1 if name == "verlet" else 2, 1, flush)
         h = pout["h_max"].cpu().numpy()
         code = pout["code"].cpu().numpy()
         esc = code == 0
