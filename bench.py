@@ -382,9 +382,9 @@ def other_paths(T, args, flush, peaks, main_sc):
         objs[name] = dict({"value": msc.npix / (ms / 1e3), "unit": UNIT, "ms_per_image": ms,
                            "workload": msc.name, "rtol": msc.rtol, "rk_step_attempts_per_image": att,
                            "roofline": fp32_roofline(att, ms, peaks)}, **h_stats(mout))
-    objs["mixed"]["arithmetic"] = ("FP32 stages, norm and control; FP64 state; double-float steps within 2 r_+ "
-                                   "and asin(0.3) of the axis; rays within 0.1 M of the critical curve traced "
-                                   "in double-float at rtol 1e-10")
+    objs["mixed"]["arithmetic"] = ("FP32 stages (theta relative to the nearest axis crossing), norm and control; "
+                                   "FP64 state; double-float steps within 1.5 r_+; rays within 0.15 M of the "
+                                   "critical curve traced in double-float at rtol 1e-10")
     objs["mixed_pair"]["arithmetic"] = objs["mixed"]["arithmetic"].replace("FP64 state", "compensated FP32-pair state")
     objs["mixed_split"]["arithmetic"] = ("the prescribed split: FP32 stages; FP64 state, error norm and step "
                                          "control; FP64 steps within 1.5 r_+; FP64 crossing refinement")

@@ -129,7 +129,7 @@ typedef struct {
  * below critical_band (in units of M) is traced entirely in double-float, as
  * TT_DOUBLE_FLOAT traces it, at rtol = atol = critical_rtol; these rays are
  * traced first, by whole warps, in the same launch.  critical_band 0 selects
- * 0.1 on TT_MIXED and TT_MIXED_PAIR and none on TT_MIXED_SPLIT, negative:
+ * 0.15 on TT_MIXED and TT_MIXED_PAIR and none on TT_MIXED_SPLIT, negative:
  * none; critical_rtol 0 selects 1e-10.  Other precisions ignore both.
  * TT_DOUBLE_FLOAT steps every ray in double-float: flow, stage points, stage
  * sums and error estimate (with double-float coefficients) and the state, with

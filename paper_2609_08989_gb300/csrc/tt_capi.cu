@@ -255,7 +255,7 @@ tt::SolverDesc make_solver(const tt_solver* s) {
     sd.refine = s->refine;
     sd.precision = s->precision;
     sd.method = s->method;
-    // near-critical rays in double-float: mixed paths only (default band 0.1 M,
+    // near-critical rays in double-float: mixed paths only (default band 0.15 M,
     // none on the prescribed split), at the FP64 path's tolerance by default
     sd.crit_band = 0.0;
     sd.crit_rtol = sd.crit_atol = 0.0;
@@ -265,7 +265,7 @@ tt::SolverDesc make_solver(const tt_solver* s) {
     sd.faults = nullptr;
 #endif
     if (mixed_precision(s->precision)) {
-        const double band_default = s->precision == TT_MIXED_SPLIT ? -1.0 : 0.1;
+        const double band_default = s->precision == TT_MIXED_SPLIT ? -1.0 : 0.15;
         const double band = s->critical_band != 0.0 ? s->critical_band : band_default;
         sd.crit_band = band > 0.0 ? band : 0.0;
         sd.crit_rtol = sd.crit_atol = s->critical_rtol > 0.0 ? s->critical_rtol : 1e-10;

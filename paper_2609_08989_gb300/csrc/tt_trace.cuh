@@ -614,7 +614,7 @@ __device__ __forceinline__ long long tile_pixel(const ImageDesc& d, long long q)
 // the cubic's three real roots), and R(r_m) / (2 r_m^2 b), b^2 = xi^2 + eta,
 // estimates the ray's distance from the critical curve in impact parameter
 // (dR/db = -2 b r^2 when xi and eta scale together).  Evaluated in FP32 (the
-// band, ~0.1 M, is ~10^6 times its rounding) from the observer's tetrad as in
+// band, ~0.15 M, is ~10^6 times its rounding) from the observer's tetrad as in
 // init_ray; the same code classifies a ray in the scan and in the main pass,
 // so every ray is traced exactly once.
 // ---------------------------------------------------------------------------

@@ -66,7 +66,7 @@ class Scene:
                                       # factor * r_h (0: 1.5 mixed, 2 on a table; < 0: none)
     fp64_pole_sin: float = 0.0        # the same, where sin(theta) < this (0 or < 0: none)
     critical_band: float = 0.0        # mixed paths: rays this close to the critical curve (units of M) are traced
-                                      # in double-float (0: 0.1, none on the prescribed split; < 0: none)
+                                      # in double-float (0: 0.15, none on the prescribed split; < 0: none)
     critical_rtol: float = 0.0        # their rtol = atol (0: 1e-10)
     # disk
     disk_enabled: int = 0

@@ -64,6 +64,25 @@ def tolerance_spread(orc, sc, pix, ref=None):
     return sr, sg
 
 
+def diverged_spread(orc, sc, pix, got, ref):
+    """tolerance_spread on the pixels whose accepted or rejected step counts
+    differ between ``got`` and ``ref``, zero on the others.  Given to compare()
+    as ``spread``, it leaves the rays that followed the oracle's step sequence
+    at ``rel`` and holds each ray that took another valid sequence (an
+    accept/reject decision within rounding of err = 1 went the other way) to
+    max(rel, SPREAD_FACTOR x its spread), the bar of the tabulated metric."""
+    pix = np.asarray(pix, dtype=np.int64)
+    sr = np.zeros(ref["r_cross"].shape)
+    sg = np.zeros(ref["g"].shape)
+    d = np.nonzero((got["steps"] != ref["steps"]) | (got["rejects"] != ref["rejects"]))[0]
+    if len(d):
+        sub = {k: (v[:, d] if v.ndim == 2 else v[d]) for k, v in ref.items()}
+        r, g = tolerance_spread(orc, sc, pix[d], sub)
+        sr[:, d] = r
+        sg[:, d] = g
+    return sr, sg
+
+
 def pixel_ab(sc, pix):
     i = pix % sc.nx
     j = pix // sc.nx
@@ -147,7 +166,7 @@ def compare(orc, sc, got, ref, pix, rel=1e-9, h_abs=1e-12, h_rel=5e-2, min_same_
             a, b = got[f][:, same], ref[f][:, same]
             zero = b == 0
             assert np.array_equal(a[zero], b[zero]), "%s: unused slots differ" % f
-            den = (np.abs(b) + peak) if f == "I_cross" else np.where(zero, 1.0, np.abs(b))
+            den = np.where(zero, 1.0, (np.abs(b) + peak) if f == "I_cross" else np.abs(b))
             ratio = np.where(zero, 0.0, np.abs(a - b) / den) / tol[:, same]
             worst[f + "_over_tol"] = float(ratio.max()) if ratio.size else 0.0
             worst[f] = float((np.where(zero, 0.0, np.abs(a - b) / den)).max()) if ratio.size else 0.0

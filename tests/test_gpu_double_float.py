@@ -31,42 +31,45 @@ def run(T, sc, **kw):
 
 # The error norm and step control run in FP32, so an accept/reject decision taken
 # within ~1e-7 of err = 1 can go the other way (~1e-4 of rays): such rays follow
-# another valid step sequence and agree to the integration's own error.
+# another valid step sequence, which differs from the oracle's by the
+# integration's own error; they are held to max(1e-9, 10 x the oracle's own
+# change at 0.5 to 2 times the tolerance), the others to 1e-9.
 # Double-float carries ~5 bits fewer than FP64: where a ray's |H| maximum is set
 # by rounding rather than truncation -- the zero-angular-momentum rays of odd
 # grids (alpha = 0 exactly), which pass through the polar axis -- it can be up to
 # 2^5 above the oracle's (12x seen); elsewhere it agrees to ~1 %.  |H| maxima are
 # compared within that factor.
-BARS = dict(rel=1e-9, rel_diverged=1e-8, min_same_steps=0.995, h_ratio_only=True, h_ratio=32.0)
+BARS = dict(rel=1e-9, min_same_steps=0.995, h_ratio_only=True, h_ratio=32.0)
+
+
+def compare_df(orc, sc, got, ref, pix):
+    return parity.compare(orc, sc, got, ref, pix, spread=parity.diverged_spread(orc, sc, pix, got, ref), **BARS)
 
 
 def test_kerr_disk_128(T, orc):
     sc = scenes.kerr_disk(128).replace(precision=scenes.DOUBLE_FLOAT)
     got = run(T, sc)
-    rep = parity.compare(orc, sc, got, orc.trace(sc), np.arange(sc.npix), **BARS)
+    rep = compare_df(orc, sc, got, orc.trace(sc), np.arange(sc.npix))
     print("double-float kerr disk 128^2:", rep)
     esc = got["code"] == 0
     assert got["h_max"][esc].max() < 1e-8
 
 
-def test_full_size_sampled(T, orc):
-    """The 1024^2 disk image with the launch shape the benchmark uses."""
+def test_full_image(T, orc):
+    """The 1024^2 disk image with the launch shape the benchmark uses, every pixel."""
     sc = scenes.kerr_disk(1024).replace(precision=scenes.DOUBLE_FLOAT)
     got = run(T, sc)
-    pix = scenes.sample_pixels(sc.npix, 2000, 41)
-    ref = orc.trace_list(sc, pix)
-    sub = {k: (v[:, pix] if v.ndim == 2 else v[pix]) for k, v in got.items()}
-    rep = parity.compare(orc, sc, sub, ref, pix, **BARS)
+    rep = compare_df(orc, sc, got, orc.trace(sc), np.arange(sc.npix))
     assert set(np.unique(got["code"])) <= {0, 1}
-    print("double-float kerr disk 1024^2 sampled:", rep)
+    print("double-float kerr disk 1024^2, every pixel:", rep)
 
 
 def test_shadow_and_ragged_range(T, orc):
     sc = scenes.schwarzschild_shadow(64).replace(precision=scenes.DOUBLE_FLOAT)
-    parity.compare(orc, sc, run(T, sc), orc.trace(sc), np.arange(sc.npix), **BARS)
+    compare_df(orc, sc, run(T, sc), orc.trace(sc), np.arange(sc.npix))
     sc = scenes.kerr_disk(97).replace(ny=83, precision=scenes.DOUBLE_FLOAT)
     got = run(T, sc, pix_begin=1234, pix_count=2345)
-    parity.compare(orc, sc, got, orc.trace(sc, pix_begin=1234, npix=2345), np.arange(1234, 1234 + 2345), **BARS)
+    compare_df(orc, sc, got, orc.trace(sc, pix_begin=1234, npix=2345), np.arange(1234, 1234 + 2345))
 
 
 def test_batch_of_uneven_images(T, orc):
@@ -75,7 +78,7 @@ def test_batch_of_uneven_images(T, orc):
     torch.cuda.synchronize()
     for sc, o in zip(imgs, outs):
         assert sc.rtol == 1e-10
-        parity.compare(orc, sc, T.to_numpy(o), orc.trace(sc), np.arange(sc.npix), **BARS)
+        compare_df(orc, sc, T.to_numpy(o), orc.trace(sc), np.arange(sc.npix))
 
 
 def test_same_steps_as_fp64_path(T):

@@ -1,8 +1,7 @@
 """Parity of the CUDA tracer (through the C ABI) with the FP64 CPU oracle.
 
-Small cases are compared on every pixel; the full-size Kerr disk image
-(1024^2, the benchmark's launch) is compared on a seeded pixel sample that the
-oracle traces one by one.
+Small cases and the full-size Kerr disk image (1024^2, the benchmark's launch)
+are compared on every pixel.
 """
 import math
 
@@ -50,17 +49,14 @@ def test_kerr_disk_256(T, orc):
     print("kerr disk 256^2:", rep)
 
 
-def test_kerr_disk_full_size_sampled(T, orc):
-    """The 1024^2 headline image, launched whole, checked on 3000 sampled pixels."""
+def test_kerr_disk_full_image(T, orc):
+    """The 1024^2 headline image with the benchmark's launch, every pixel."""
     sc = scenes.kerr_disk(1024)
     got = run(T, sc)
-    pix = scenes.sample_pixels(sc.npix, 3000, 17)
-    ref = orc.trace_list(sc, pix)
-    sub = {k: (v[:, pix] if v.ndim == 2 else v[pix]) for k, v in got.items()}
-    rep = parity.compare(orc, sc, sub, ref, pix)
+    rep = parity.compare(orc, sc, got, orc.trace(sc), np.arange(sc.npix))
     # every pixel finished with a physical code
     assert set(np.unique(got["code"])) <= {0, 1}
-    print("kerr disk 1024^2 sampled:", rep)
+    print("kerr disk 1024^2, every pixel:", rep)
 
 
 def test_fp64_h_bound(T, orc):

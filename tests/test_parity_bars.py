@@ -63,3 +63,29 @@ def test_planted_error_fails(orc, kind, rtol):
     with pytest.raises(AssertionError):
         parity.compare(orc, sc, bad, ref, pix, rel=1e-9, min_same_steps=0.0, spread=spread,
                        h_ratio_only=True, h_ratio=10.0)
+
+
+def test_diverged_spread_only_on_diverged_rays(orc):
+    """The spread bar for the rays of an FP64-equivalent path whose step sequence
+    left the oracle's: it is the oracle's tolerance spread on exactly those rays,
+    and the rays that kept the oracle's sequence stay at 1e-9 (an error of 5e-9
+    planted in one of their crossings fails)."""
+    sc = scenes.kerr_disk(24)
+    pix = np.arange(sc.npix)
+    ref = orc.trace(sc)
+    got = {k: v.copy() for k, v in ref.items()}
+    hit = np.nonzero(ref["n_cross"] > 0)[0]
+    d = hit[:5]
+    got["rejects"][d] += 1
+    sr, sg = parity.diverged_spread(orc, sc, pix, got, ref)
+    full_r, full_g = parity.tolerance_spread(orc, sc, pix, ref)
+    mask = np.zeros(sc.npix, bool)
+    mask[d] = True
+    assert np.all(sr[:, ~mask] == 0) and np.all(sg[:, ~mask] == 0)
+    assert np.array_equal(sr[:, mask], full_r[:, mask]) and np.array_equal(sg[:, mask], full_g[:, mask])
+    assert sr[0, d].min() > 0
+    parity.compare(orc, sc, got, ref, pix, rel=1e-9, spread=(sr, sg))
+    bad = {k: v.copy() for k, v in got.items()}
+    bad["r_cross"][0, hit[10]] *= 1.0 + 5e-9
+    with pytest.raises(AssertionError):
+        parity.compare(orc, sc, bad, ref, pix, rel=1e-9, spread=(sr, sg))
