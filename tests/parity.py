@@ -31,9 +31,12 @@ import numpy as np
 import kerr_exact as KE
 
 FIELDS = ("r_cross", "g", "I_cross")
-# Allowed multiple of the oracle's own tolerance spread (largest ratio seen for
-# a third valid integration: 3.3 on the table images at rtol 1e-10 and 1e-12).
-SPREAD_FACTOR = 10.0
+# Allowed multiple of the oracle's own tolerance spread.  Largest ratio seen for
+# a third valid integration (the oracle with its camera moved by 1e-15 or
+# 3e-15): 3.3 on the 40^2 table images at rtol 1e-10 and 1e-12, 18.4 on the
+# 1,048,576 rays of the 1024^2 extrapolator image (the tail grows with the
+# number of rays: one ray in a million beyond 10).
+SPREAD_FACTOR = 30.0
 
 
 def _rel(x, ref, f):
@@ -48,10 +51,7 @@ SPREAD_TOLERANCES = (0.5, 0.7, 1.4, 2.0)
 def tolerance_spread(orc, sc, pix, ref=None):
     """Per crossing (3 x n): the largest relative change of the oracle's r and g
     when its tolerance is scaled by 0.5, 0.7, 1.4 or 2 (0 where a run changes
-    the pixel's code or crossing count, or where there is no crossing).  With
-    these four, a third valid integration (inputs moved by 1e-15) stays within
-    3.3 times the spread on the table images (a single halving and doubling
-    can both land close to the reference by chance: 9.7 times seen)."""
+    the pixel's code or crossing count, or where there is no crossing)."""
     pix = np.asarray(pix, dtype=np.int64)
     if ref is None:
         ref = orc.trace_list(sc, pix)
@@ -62,6 +62,26 @@ def tolerance_spread(orc, sc, pix, ref=None):
         sr = np.maximum(sr, _rel(x, ref, "r_cross"))
         sg = np.maximum(sg, _rel(x, ref, "g"))
     return sr, sg
+
+
+def h_image_stats(got, ref, q_rel=0.05, max_ratio=3.0):
+    """|H| of the escaped rays compared as image statistics, for an integrator
+    whose per-ray maximum is set by single steps whose error estimate cancels
+    (the extrapolator: two valid step sequences at the same tolerance put a
+    ray's maximum up to ~100x apart): the median, 99th and 99.9th percentiles
+    within q_rel (relative) of the oracle's, the image maximum within
+    max_ratio.  The oracle against itself (camera moved by 1e-15) keeps them
+    within 0.5 % and 0.48-1.23x; at twice its tolerance the median moves 3.2x."""
+    def stats(o):
+        e = o["h_max"][o["code"] == 0]
+        return np.array([np.median(e), np.percentile(e, 99), np.percentile(e, 99.9), e.max()])
+    g, r = stats(got), stats(ref)
+    q = np.abs(g[:3] / r[:3] - 1.0)
+    m = max(g[3] / r[3], r[3] / g[3])
+    out = {"h_median_p99_p999_rel": [float(x) for x in q], "h_max_ratio_image": float(m)}
+    assert np.all(q <= q_rel), "escaped |H| quantiles off by %s" % q
+    assert m <= max_ratio, "escaped |H| image maximum off by %.3g x" % m
+    return out
 
 
 def diverged_spread(orc, sc, pix, got, ref):
@@ -114,7 +134,7 @@ def in_band(orc, sc, pix, width=None):
 
 
 def compare(orc, sc, got, ref, pix, rel=1e-9, h_abs=1e-12, h_rel=5e-2, min_same_steps=0.98, report=None,
-            rel_diverged=None, h_ratio_only=False, h_ratio=2.0, spread=None):
+            rel_diverged=None, h_ratio_only=False, h_ratio=2.0, spread=None, h_per_ray=True):
     """got/ref: dicts of numpy arrays for pixel indices pix (same order).
 
     h_ratio_only: compare every |H| maximum within a factor 2 (used for the
@@ -126,7 +146,8 @@ def compare(orc, sc, got, ref, pix, rel=1e-9, h_abs=1e-12, h_rel=5e-2, min_same_
     None means such rays get ``rel`` too.
     spread: (r, g) arrays from tolerance_spread; every crossing then gets
     max(rel, SPREAD_FACTOR x its spread) (r and I_cross with the r spread, g
-    with the g spread), whatever its step counts."""
+    with the g spread), whatever its step counts.
+    h_per_ray: False skips the per-ray |H| comparisons (see h_image_stats)."""
     pix = np.asarray(pix)
     n = len(pix)
     code_bad = np.nonzero(got["code"] != ref["code"])[0]
@@ -211,9 +232,11 @@ def compare(orc, sc, got, ref, pix, rel=1e-9, h_abs=1e-12, h_rel=5e-2, min_same_
     # Captured rays end at r ~ r_h (1 + 1e-3), where p_r ~ 1/(r - r_h) turns
     # relative state noise of ~1e-13 into ~1e-8 of H: agreement within 2x.
     esc = ok & (ref["code"] == 0) & ~(diverged & (rel_diverged is not None))
-    if h_ratio_only:
+    if h_ratio_only or not h_per_ray:
         esc = esc & False
     oth = ok & ~esc
+    if not h_per_ray:
+        oth = oth & False
     dh = np.abs(got["h_max"][esc] - ref["h_max"][esc])
     lim = h_abs + h_rel * np.abs(ref["h_max"][esc])
     worst["h_max_excess_escaped"] = float((dh / lim).max()) if dh.size else 0.0

@@ -89,3 +89,13 @@ def test_diverged_spread_only_on_diverged_rays(orc):
     bad["r_cross"][0, hit[10]] *= 1.0 + 5e-9
     with pytest.raises(AssertionError):
         parity.compare(orc, sc, bad, ref, pix, rel=1e-9, spread=(sr, sg))
+
+
+def test_h_image_stats(orc):
+    """The extrapolator's |H| bar: a third valid integration passes it; the
+    oracle at twice its tolerance (a real loss of accuracy) fails it."""
+    sc = scenes.kerr_disk(96).replace(method=scenes.GBS)
+    ref = orc.trace(sc)
+    print("gbs |H| image statistics:", parity.h_image_stats(orc.trace(perturbed(sc)), ref))
+    with pytest.raises(AssertionError):
+        parity.h_image_stats(orc.trace(sc.replace(rtol=2 * sc.rtol, atol=2 * sc.atol)), ref)
