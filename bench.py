@@ -114,6 +114,10 @@ def parse():
                    help="skip the objects of the other four integrators in the default line")
     p.add_argument("--shard", action="store_true",
                    help="N ranks split one image by pixel ranges balanced by a previous trace's step counts")
+    p.add_argument("--critical-band", type=float, default=None,
+                   help="mixed paths: near-critical band in M (negative: no escalation; default: the library's)")
+    p.add_argument("--zone-factor", type=float, default=None,
+                   help="mixed paths: extended-precision zone radius in r_+ (negative: none; default: the library's)")
     p.add_argument("--workload", default="kerr_disk", choices=["kerr_disk", "batch", "table", "e3", "e5", "osiris"],
                    help="kerr_disk: the 1024^2 headline image (default); batch: 64 uneven images in one "
                         "persistent launch, replayed from a CUDA graph; table: the 4096^2 tabulated-metric image")
@@ -168,7 +172,8 @@ def time_variant(T, sc, steps, warmup, flush, tune=None):
 
 
 def config_dict(sc, world, shard=False):
-    return {"workload": sc.name, "nx": sc.nx, "ny": sc.ny, "a": sc.a,
+    extra = {k: v for k, v in (("critical_band", sc.critical_band), ("zone_factor", sc.fp64_radius_factor)) if v != 0.0}
+    return {**extra, "workload": sc.name, "nx": sc.nx, "ny": sc.ny, "a": sc.a,
             "theta_obs_deg": round(math.degrees(sc.theta_obs), 6),
             "r_obs": sc.r_obs, "field": [sc.alpha_min, sc.alpha_max], "rtol": sc.rtol, "atol": sc.atol,
             "integrator": METHOD_NAMES[sc.method], "disk": ["isco", sc.r_out], "max_crossings": sc.max_crossings,
@@ -480,6 +485,10 @@ def run_tartarus(args):
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     sc = workload(args.n, args.precision, args.method)
+    if args.critical_band is not None:
+        sc = sc.replace(critical_band=args.critical_band)
+    if args.zone_factor is not None:
+        sc = sc.replace(fp64_radius_factor=args.zone_factor)
     T.lib()
     peaks = measure_peaks(local)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
