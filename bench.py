@@ -77,6 +77,8 @@ FP64_ISSUED_PER_STEP = (260.7, 202.6, 19.5)
 # FP32 thread instructions (FFMA + FMUL + FADD) per double-float step attempt, from ncu's
 # instruction counts on the 512^2 image
 DF_FP32_INST_PER_STEP = 4693
+# the same for the double-float kernel on the tabulated metric (256^2 image of its scene)
+TABLE_DF_FP32_INST_PER_STEP = 15398
 # the same per step attempt of the mixed-pair kernel on the 1024^2 image (its FP32 steps with
 # the zone and near-critical double-float steps amortised over all attempts)
 MIXED_FP32_INST_PER_STEP = 837
@@ -439,6 +441,32 @@ def other_paths(T, args, flush, peaks, main_sc):
                                % graph.launches_per_replay,
                      "rk_step_attempts": batt, "h_max_escaped": hesc,
                      "roofline": fp32_roofline(batt, ms, peaks)}
+    # the tabulated-metric image (C5): Kerr a = 0.998 sampled on a 512 x 256 grid, the
+    # 4096^2 camera at rtol 1e-12, traced in double-float (one warm-up, one timed launch)
+    tsc = scenes.table_kerr_with_nodes(4 * args.n).replace(precision=scenes.DOUBLE_FLOAT)
+    table = T.Table(tsc.table, tsc.r_min, tsc.r_max)
+    tout = T.alloc_outputs(tsc.npix)
+    T.trace(tsc, out=tout, table=table, stream=stream)
+    torch.cuda.synchronize()
+    flush.fill_(3)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    T.trace(tsc, out=tout, table=table, stream=stream)
+    b.record(stream)
+    torch.cuda.synchronize()
+    tms = a.elapsed_time(b)
+    tatt = attempts_of(tout)
+    tinst = TABLE_DF_FP32_INST_PER_STEP * tatt / (tms / 1e3)
+    objs["table"] = dict({"value": tsc.npix / (tms / 1e3), "unit": UNIT, "ms_per_image": tms, "workload": tsc.name,
+                          "a": tsc.a, "table": [512, 256], "rtol": tsc.rtol, "precision": "double_float",
+                          "rk_step_attempts_per_image": tatt,
+                          "fp32_pipe": {"instructions_per_step": TABLE_DF_FP32_INST_PER_STEP,
+                                        "frac": tinst / (peaks["fp32"] / 2 * 1e12),
+                                        "source": "FP32 thread instructions per step from ncu's instruction counts "
+                                                  "(256^2 image of this scene) over the FMA rate measured in this run"},
+                          "note": "one timed launch after one warm-up; the FP64 path on this image: "
+                                  "bench.py --workload table"}, **h_stats(tout))
+    del tout, table
     # equal accuracy: the FP64 and double-float paths on the mixed paths' 2048^2 image at the
     # loosest tolerance that also keeps |H| <= 1e-6 on escaped rays and crossings within 1e-5
     eqa = {}
