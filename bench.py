@@ -301,8 +301,8 @@ def run_reference(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": cfg,
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-                             "sample": "%d seeded random pixels of the %dx%d image, all host cores"
-                                       % (tot_rays, sc.nx, sc.ny)},
+                             "sample": "%d seeded random pixels of the %dx%d image in chunks of distinct pixels, "
+                                       "all host cores" % (tot_rays, sc.nx, sc.ny)},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
