@@ -1,7 +1,8 @@
 """The paper's own scenes traced on the GPU through the C ABI, against the
 oracle: the Fig. 3 Kerr disk image with and without the Doppler factor
 (Sec. 4.2), the Table 1 Schwarzschild disk (Sec. 4.3) and the OSIRIS
-calibration shadow (Sec. 4.3); plus the image-product helpers on a GPU render."""
+calibration shadow (Sec. 4.3), small and at the benchmark's 1024^2 (every
+pixel); plus the image-product helpers on a GPU render."""
 import json
 
 import numpy as np
@@ -41,6 +42,16 @@ def test_e5_and_osiris_parity(T, orc):
     for sc in (scenes.schwarzschild_e5(64), scenes.osiris_scene(64)):
         rep = parity.compare(orc, sc, run(T, sc), orc.trace(sc), np.arange(sc.npix))
         print(sc.name, rep)
+
+
+@pytest.mark.parametrize("make", [scenes.kerr_e3, scenes.schwarzschild_e5, scenes.osiris_scene],
+                         ids=["e3", "e5", "osiris"])
+def test_scene_full_image_1024(T, orc, make):
+    """The scenes at the 1024^2 size the benchmark times them at, every pixel."""
+    sc = make(1024)
+    got = run(T, sc)
+    rep = parity.compare(orc, sc, got, orc.trace(sc), np.arange(sc.npix))
+    print(sc.name, "1024^2, every pixel:", rep)
 
 
 def test_e3_products(T, tmp_path):
