@@ -32,7 +32,7 @@ def run(T, sc, **kw):
 # The error norm and step control run in FP32, so an accept/reject decision taken
 # within ~1e-7 of err = 1 can go the other way (~1e-4 of rays): such rays follow
 # another valid step sequence, which differs from the oracle's by the
-# integration's own error; they are held to max(1e-9, 10 x the oracle's own
+# integration's own error; they are held to max(1e-9, 30 x the oracle's own
 # change at 0.5 to 2 times the tolerance), the others to 1e-9.
 # Double-float carries ~5 bits fewer than FP64: where a ray's |H| maximum is set
 # by rounding rather than truncation -- the zero-angular-momentum rays of odd
@@ -93,7 +93,7 @@ def test_same_steps_as_fp64_path(T):
 # The tabulated metric, at the FP64 table path's bars: the interpolated flow
 # (its slopes cancel ~10^3-fold) carries rounding that moves the step sizes, so
 # two correct implementations take different valid step sequences, which differ
-# by the integration's own error; every crossing is held to max(1e-9, 10 x the
+# by the integration's own error; every crossing is held to max(1e-9, 30 x the
 # oracle's own change at 0.5 to 2 times the tolerance).
 # |H| maxima: at rtol 1e-12 a ray's drift off H = 0 is set by the rounding of
 # the interpolated flow, which carries the pair's 2^-48 instead of 2^-53, so the

@@ -37,7 +37,7 @@ def test_table_4096_sampled(T, orc):
     pix = scenes.sample_pixels(sc.npix, 600, 59)
     ref = orc.trace_list(sc, pix)
     sub = {k: (v[:, pix] if v.ndim == 2 else v[pix]) for k, v in got.items()}
-    # the bars of the small table test: max(1e-9, 10 x the oracle's own tolerance
+    # the bars of the small table test: max(1e-9, 30 x the oracle's own tolerance
     # spread) per crossing
     spread = parity.tolerance_spread(orc, sc, pix, ref)
     rep = parity.compare(orc, sc, sub, ref, pix, rel=1e-9, min_same_steps=0.0, spread=spread,

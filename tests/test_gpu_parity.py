@@ -168,10 +168,29 @@ def table_scene(orc, n, rtol=1e-12):
 # step sequences at the same tolerance differ by the integration's own error:
 # ~1e-8 on primary crossings, ~1e-7 on higher orders, at rtol 1e-10 as at 1e-12
 # (the oracle against itself at 0.5 to 2 times the tolerance).  Every crossing
-# is held to max(1e-9, 10 x that spread of the oracle, measured per crossing).
+# is held to max(1e-9, 30 x that spread of the oracle, measured per crossing).
 # Step counts: at rtol 1e-10 three quarters of the rays take as many accepted
 # and rejected steps as the oracle (77 % measured); at rtol 1e-12 almost none do.
 TABLE_SAME_STEPS = {1e-10: 0.7, 1e-12: 0.0}
+
+
+@pytest.fixture(scope="module")
+def table256(orc):
+    sc = table_scene(orc, 256)
+    ref = orc.trace(sc)
+    return sc, ref, parity.tolerance_spread(orc, sc, np.arange(sc.npix), ref)
+
+
+@pytest.mark.parametrize("precision", [scenes.FP64, scenes.DOUBLE_FLOAT])
+def test_table_256_every_pixel(T, orc, table256, precision):
+    """The tabulated metric at its benchmark tolerance (rtol 1e-12), 65,536 rays,
+    FP64 and double-float, every pixel at the bar above."""
+    sc, ref, spread = table256
+    sc = sc.replace(precision=precision)
+    got = run(T, sc)
+    rep = parity.compare(orc, sc, got, ref, np.arange(sc.npix), rel=1e-9, min_same_steps=0.0, spread=spread,
+                         h_ratio_only=True, h_ratio=10.0 if precision == scenes.FP64 else 64.0)
+    print("table 256^2 precision %d, every pixel:" % precision, rep)
 
 
 @pytest.mark.parametrize("rtol", [1e-12, 1e-10])

@@ -1,5 +1,5 @@
 """The parity bar for integrations whose step sequence is not fixed to rounding
-(tabulated metric, extrapolator): every crossing within max(1e-9, 10 x the
+(tabulated metric, extrapolator): every crossing within max(1e-9, 30 x the
 oracle's own change at 0.5 to 2 times the tolerance).  Checked on the CPU with
 the oracle alone: a third valid integration (the same scene with its camera
 moved by 1e-15 relative) passes the bar, and an error planted in the crossing
