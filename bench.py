@@ -48,10 +48,11 @@ FP32_PEAK_DERIVED = SM_COUNT * SM_MAX_MHZ * 1e6 * 128 * 2 / 1e12
 # counted from the kernel source of this build (FMA = 2; add, mul, reciprocal and
 # sqrt 1 each, the reciprocal's Newton refinement not counted; sin and cos 1 each,
 # however they are evaluated -- here by angle addition from the step start):
-# 6 flow evaluations x 55 + stage combinations 226 (stages 2-4 with h-scaled
-# coefficients) + error norm 30 (one shared reciprocal) + step control 5.
+# 6 flow evaluations x 55 + stage combinations and error sum 222 (stages 2-4 with
+# h-scaled coefficients; the error vector without its factor h) + error norm 30 (one
+# shared reciprocal) + 1 (h applied to that reciprocal) + step control 5.
 FLOW_FLOPS, NORM_FLOPS, CONTROL_FLOPS = 55, 30, 5
-FLOPS_PER_STEP = 6 * FLOW_FLOPS + 226 + NORM_FLOPS + CONTROL_FLOPS
+FLOPS_PER_STEP = 6 * FLOW_FLOPS + 222 + NORM_FLOPS + 1 + CONTROL_FLOPS
 # Cash-Karp and Fehlberg also evaluate the flow six times per step attempt (five
 # stages and the new point); their stage sums have one (Fehlberg: e_7 = 0) or two
 # (Cash-Karp: b_5 = e_7 = 0) fewer FMA per state component.
@@ -73,7 +74,7 @@ METHOD_NAMES = {v: k for k, v in METHODS.items()}
 FLOPS_PER_STEP_F32 = 6 * 72 + 232 + 20 + 5
 # FP64 thread instructions per Dormand-Prince step attempt of the FP64 kernel, from ncu's
 # instruction counts on the 512^2 image (7.02e7 attempts): DFMA, DMUL, DADD
-FP64_ISSUED_PER_STEP = (260.7, 202.6, 19.5)
+FP64_ISSUED_PER_STEP = (260.8, 199.6, 19.5)
 # FP32 thread instructions (FFMA + FMUL + FADD) per double-float step attempt, from ncu's
 # instruction counts on the 512^2 image
 DF_FP32_INST_PER_STEP = 4693
@@ -84,9 +85,9 @@ TABLE_DF_FP32_INST_PER_STEP = 15398
 MIXED_FP32_INST_PER_STEP = 837
 BYTES_OUT_PER_PIXEL = 3 * 3 * 8 + 8 + 8 + 4 + 4 + 1 + 1
 # DRAM traffic of the FP64 tracer per launch on the 1024^2 image: ncu's
-# dram__bytes_read.sum + dram__bytes_write.sum of one full-size launch (1.6 MB read,
-# 49.8 MB written: part of the 103 MB of outputs leaves the L2 during the kernel)
-TRAFFIC_BYTES_1024 = 1635840 + 49813504
+# dram__bytes_read.sum + dram__bytes_write.sum of one full-size launch (2.6 MB read,
+# 51.2 MB written: part of the 103 MB of outputs leaves the L2 during the kernel)
+TRAFFIC_BYTES_1024 = 2555392 + 51188480
 # host-to-device input of one step: the launch's parameter block (sizeof(tt::LaunchParams<1>):
 # solver settings, launch shape and the image descriptor)
 DESC_BYTES = 728

@@ -51,7 +51,8 @@ __device__ __forceinline__ double step_factor(double err2) {
 
 // ---------------------------------------------------------------------------
 // One step of an embedded 5(4) pair in FP64 (paper Sec. 3.2): returns the
-// fifth-order point yn, the flow kn and H there, and the error vector.  For
+// fifth-order point yn, the flow kn and H there, and the error vector divided
+// by h.  For
 // Dormand-Prince kn is the seventh stage (first same as last); for Cash-Karp
 // and Fehlberg it is evaluated after the six stages.
 // ---------------------------------------------------------------------------
@@ -114,8 +115,9 @@ __device__ __forceinline__ void rk_step64(const ImageDesc& d, const KerrK& kk, c
         *sn = ss;
         *cn = cs;
     }
+// the error vector without its factor h (err_norm2 applies it once)
 #define TT_E(f) \
-    h * TT_MAC(T::e7, kn.f, fma(T::e6, k6.f, fma(T::e5, k5.f, fma(T::e4, k4.f, fma(T::e3, k3.f, T::e1 * k1.f)))))
+    TT_MAC(T::e7, kn.f, fma(T::e6, k6.f, fma(T::e5, k5.f, fma(T::e4, k4.f, fma(T::e3, k3.f, T::e1 * k1.f)))))
     err.r = TT_E(r);
     err.th = TT_E(th);
     err.pr = TT_E(pr);
@@ -275,8 +277,10 @@ __device__ __forceinline__ double sq3(double a, double b, double c) {
 // refined by a single Newton step (~1e-14 relative: the norm only decides
 // err <= 1 and scales the step).  A product outside the normal range (tolerances
 // near 1e-75 or 1e75) takes the per-component reciprocals instead.
+// The error vector is he * e (he = h for the Runge-Kutta pairs, whose e omits
+// the step's factor h; 1 otherwise).
 __device__ __forceinline__ double err_norm2(const State& y, const State& yn, const State& e,
-                                            double atol, double rtol) {
+                                            double atol, double rtol, double he) {
     const double s0 = fma(rtol, fmax(fabs(y.r), fabs(yn.r)), atol);
     const double s1 = fma(rtol, fmax(fabs(y.th), fabs(yn.th)), atol);
     const double s2 = fma(rtol, fmax(fabs(y.pr), fabs(yn.pr)), atol);
@@ -286,14 +290,15 @@ __device__ __forceinline__ double err_norm2(const State& y, const State& yn, con
     // outside [2^-930, 2^930] (the exponent field, on the integer pipe)
     const int ex = (__double2hiint(pp) >> 20) & 0x7ff;
     if (ex < 1023 - 930 || ex > 1023 + 930) {
-        const double q3 = err_ratio(e.pth, y.pth, yn.pth, atol, rtol);
-        return 0.25 * fma(q3, q3, sq3(err_ratio(e.r, y.r, yn.r, atol, rtol), err_ratio(e.th, y.th, yn.th, atol, rtol),
-                                      err_ratio(e.pr, y.pr, yn.pr, atol, rtol)));
+        const double q3 = err_ratio(he * e.pth, y.pth, yn.pth, atol, rtol);
+        return 0.25 * fma(q3, q3, sq3(err_ratio(he * e.r, y.r, yn.r, atol, rtol),
+                                      err_ratio(he * e.th, y.th, yn.th, atol, rtol),
+                                      err_ratio(he * e.pr, y.pr, yn.pr, atol, rtol)));
     }
     double inv;
     asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(inv) : "d"(pp));
-    inv = fma(inv, fma(-pp, inv, 1.0), inv);
-    const double i01 = inv * p23, i23 = inv * p01;   // 1/(s0 s1), 1/(s2 s3)
+    inv = fma(inv, fma(-pp, inv, 1.0), inv) * he;
+    const double i01 = inv * p23, i23 = inv * p01;   // he/(s0 s1), he/(s2 s3)
     const double q0 = (e.r * s1) * i01, q1 = (e.th * s0) * i01;
     const double q2 = (e.pr * s3) * i23, q3 = (e.pth * s2) * i23;
     return 0.25 * fma(q3, q3, fma(q2, q2, fma(q1, q1, q0 * q0)));
@@ -923,7 +928,7 @@ __device__ int step_ray64(Lane& L, const SolverDesc& sol) {
         rk_step64<METRIC, METHOD>(d, L.kk, L.R, L.y, L.k1, L.h, yn, kn, Hn, e, L.s0, L.c0, &sn, &cn);
     }
     // Verlet: fixed step, always accepted
-    const double err2 = (METHOD == 4) ? 0.0 : err_norm2(L.y, yn, e, sol.atol, sol.rtol);
+    const double err2 = (METHOD == 4) ? 0.0 : err_norm2(L.y, yn, e, sol.atol, sol.rtol, METHOD == 3 ? 1.0 : L.h);
     if (nan_bits(err2) | nonfinite_bits(yn.r) | nonfinite_bits(yn.th) | nonfinite_bits(yn.pr) |
         nonfinite_bits(yn.pth))
         return 4;
@@ -1063,7 +1068,7 @@ __device__ int step_ray32(Lane& L, StateF& yhi, const SolverDesc& sol) {
         y64n = State{L.y.r + (double)inc.r, L.y.th + (double)inc.th, L.y.pr + (double)inc.pr,
                      L.y.pth + (double)inc.pth};
         const State e64 = State{(double)TT_E(r), (double)TT_E(th), (double)TT_E(pr), (double)TT_E(pth)};
-        err64 = err_norm2(L.y, y64n, e64, sol.atol, sol.rtol);
+        err64 = err_norm2(L.y, y64n, e64, sol.atol, sol.rtol, 1.0);
         err2 = nan_bits(err64) ? __int_as_float(0x7fffffff) : (err64 <= 1.0 ? 0.0f : 2.0f);
     } else {
         const float atol = (float)sol.atol, rtol = (float)sol.rtol;
