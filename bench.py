@@ -82,7 +82,7 @@ DF_FP32_INST_PER_STEP = 4693
 TABLE_DF_FP32_INST_PER_STEP = 15398
 # the same per step attempt of the mixed-pair kernel on the 1024^2 image (its FP32 steps with
 # the zone and near-critical double-float steps amortised over all attempts)
-MIXED_FP32_INST_PER_STEP = 837
+MIXED_FP32_INST_PER_STEP = 889
 BYTES_OUT_PER_PIXEL = 3 * 3 * 8 + 8 + 8 + 4 + 4 + 1 + 1
 # DRAM traffic of the FP64 tracer per launch on the 1024^2 image: ncu's
 # dram__bytes_read.sum + dram__bytes_write.sum of one full-size launch (2.6 MB read,
